@@ -720,7 +720,8 @@ template <class R> inline bool solve3(R J[3][3], R b[3], R d[3]) {
 // One backward-Euler substep y - y^n - dt f(y) = 0 by Newton's method with a forward-
 // difference Jacobian (relative step 1e-7; abundance steps floored at 1e-17) and
 // fraction-to-boundary damping that keeps T_mu, x_H2, x_H+ and x_H positive.  Converged
-// when every full (undamped) step satisfies |d_i| <= rtol |y_i| (+1e-30 for abundances).
+// when every full (undamped) step satisfies |d_i| <= rtol |y_i| (READING: relative for
+// every component, so abundances as small as 1e-25 are still converged relatively).
 // Returns the iteration count, or -1 on failure.
 template <class R> int newton_substep(const CellIn& c, const Params& p, const Pre<R>& P, R mu, const R* yn, R dts,
                                       const R* seed, R* y) {
@@ -758,7 +759,7 @@ template <class R> int newton_substep(const CellIn& c, const Params& p, const Pr
     for (int i = 0; i < 3; ++i) {
       R step = lam * d[i];
       y[i] = y[i] + step;
-      R tol = R(p.newton_rtol) * rabs(y[i]) + ((i == 0) ? R(0.0) : R(1e-30));
+      R tol = R(p.newton_rtol) * rabs(y[i]) + R(1e-300);
       if (rabs(step) > tol) conv = false;
     }
     if (!finite_(y[0]) || !finite_(y[1]) || !finite_(y[2])) return -1;
