@@ -64,9 +64,9 @@ class Params(ctypes.Structure):
 
 def default_params(mode: int = 0, **kw) -> Params:
     """Defaults: |dv/dr| = 1 km/s/pc, T_CMB = 2.73 K, chi0 = 1, E_OPT,0 = E_FUV,0,
-    tau_OPT = tau_PE/3 (Sec. 4.3.6), limiter 0.1 (Sec. 6.1), FD step 1e-4, Newton
+    tau_OPT = tau_PE/3 (Sec. 4.3.6), limiter 0.1 (Sec. 6.1), FD step 1e-3 (READING), Newton
     rtol 1e-12 (50 iterations), T floor 1 K, at most 10^6 substeps."""
-    p = Params(1.0, 2.73, 1.0, 1.0, 1.0 / 3.0, 0.1, 1e-4, 1e-12, 1.0, 50, 1000000, mode, 0)
+    p = Params(1.0, 2.73, 1.0, 1.0, 1.0 / 3.0, 0.1, 1e-3, 1e-12, 1.0, 50, 1000000, mode, 0)
     for k, v in kw.items():
         setattr(p, k, v)
     return p

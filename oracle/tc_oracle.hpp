@@ -644,16 +644,21 @@ template <class R> CellOut step_paper(const CellIn& c, const Params& p, double T
     R DH2 = R(1.65) * r.zcrH2 + P.zpd + P.zpiH2 + r.zcd;
     R I = P.zpiH + r.zcrH + r.zci;
     R Rr = r.arr * q.xe * P.n + r.agr * P.n;
-    // (I - A dt) X' = X + b dt with A = [[-(2kn+D), -kn], [-2I, -(I+R)]], b = (kn, I)
-    R m11 = R(1.0) + (R(2.0) * kn + DH2) * dts;
-    R m12 = kn * dts;
-    R m21 = R(2.0) * I * dts;
-    R m22 = R(1.0) + (I + Rr) * dts;
-    R r1 = xH2 + kn * dts;
-    R r2 = xHp + I * dts;
-    R det = m11 * m22 - m12 * m21;
-    xH2 = (r1 * m22 - m12 * r2) / det;
-    xHp = (m11 * r2 - m21 * r1) / det;
+    // (I - A dt) X' = X + b dt with A = [[-(2kn+D), -kn], [-2I, -(I+R)]], b = (kn, I),
+    // solved by Cramer's rule.  With a = 2kn + D and c = I + R the determinant and the
+    // two numerators expand to sums of non-negative terms:
+    //   det = 1 + (a + c) dt + (2 kn R + D c) dt^2
+    //   num_H2 = x_H2 (1 + c dt) + kn dt (1 - x_H+ + R dt)
+    //   num_H+ = x_H+ (1 + a dt) + I dt (1 - 2 x_H2 + D dt)
+    // (algebraically identical to m22 r1 - m12 r2 etc., but free of the cancellation of
+    // two large products when I dt >> 1), which also shows X' >= 0.
+    R a = R(2.0) * kn + DH2;
+    R cc = I + Rr;
+    R det = R(1.0) + (a + cc) * dts + (R(2.0) * kn * Rr + DH2 * cc) * dts * dts;
+    R num2 = xH2 * (R(1.0) + cc * dts) + kn * dts * ((R(1.0) - xHp) + Rr * dts);
+    R nump = xHp * (R(1.0) + a * dts) + I * dts * ((R(1.0) - R(2.0) * xH2) + DH2 * dts);
+    xH2 = num2 / det;
+    xHp = nump / det;
     Tmu = Tmu_new;
     // Re-equilibrate C/O/e at (T^{n+1}, X^{n+1}) and update mu.
     q = equilibrium(c, P, Tn1, xH2, xHp);
