@@ -1,0 +1,138 @@
+/*
+ * tc.h -- C ABI of the GB300 thermochemistry source-step library.
+ *
+ * The library advances, cell by cell, the thermochemistry source step of Kim, Gong,
+ * Kim & Ostriker (2023, arXiv:2210.08024), Sec. 6.1: with density and radiation frozen
+ * over a time step dt, it subcycles the internal energy (through T_mu = T/mu) and the
+ * non-equilibrium abundances x_H2 and x_H+ (Eqs. e:ODE1, e:ODE2), putting C+, CO, C, O,
+ * O+ and the electrons in equilibrium after every substep (Secs. 3.2, 3.3) and using the
+ * paper's rate coefficients (Sec. 3), heating (Sec. 4.1-4.4) and cooling (Sec. 4.3).
+ *
+ * Conventions
+ *  - All functions return int: TC_OK (0) or a negative TC_E* code.  No C++ exception
+ *    crosses this boundary.  tc_strerror() names a code.
+ *  - Field arrays are caller-owned DEVICE pointers (SoA, FP64, length ncell, 8-byte
+ *    aligned; 16-byte alignment lets the kernel use paired loads).  The library never
+ *    frees or retains them after the call's kernels complete.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  All
+ *    device work is stream-ordered; tc_step does not synchronise.
+ *  - Per-cell numerical trouble (substep cap reached, Newton failure, non-finite state)
+ *    does not fail the call: it is reported in the optional per-cell status array.
+ *  - A handle is not thread-safe; use one handle per stream.
+ *  - Only tc_step_host takes host pointers (it copies, runs and copies back).
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----- return codes */
+#define TC_OK 0
+#define TC_EINVAL (-1)    /* bad argument: NULL required pointer, ncell < 0, misalignment, bad mode */
+#define TC_ECUDA (-2)     /* a CUDA runtime call failed; the sticky error is left to the caller */
+#define TC_ENOMEM (-3)    /* device or host allocation failed */
+#define TC_ENOMLP (-4)    /* seeded mode requested before tc_load_mlp */
+#define TC_ENODEV (-5)    /* no sm_103 device visible */
+
+/* ----- integration modes */
+#define TC_MODE_PAPER_FP64 0   /* the paper's sequential update (Sec. 6.1), FP64 throughout */
+#define TC_MODE_NEWTON_FP64 1  /* coupled backward Euler on (T_mu, x_H2, x_H+) by Newton, FP64 */
+#define TC_MODE_MIXED 2        /* as TC_MODE_NEWTON_FP64, source terms in FP32, Newton in FP64 */
+#define TC_MODE_MIXED_SEEDED 3 /* as TC_MODE_MIXED, each Newton solve seeded by the MLP */
+#define TC_MODE_NEWTON_FP64_SEEDED 4 /* as TC_MODE_NEWTON_FP64, MLP-seeded */
+
+/* ----- physics switches (tc_params.flags) */
+#define TC_CONST_KGR 1u  /* k_gr = 3e-17 Z'_d (the paper's test setting, Sec. 7) instead of Eq. e:H2form */
+#define TC_NO_ROVIB 2u   /* H2 ro-vibrational cooling off (Sec. 7.1.2 comparison) */
+#define TC_NO_CIE 4u     /* He + metal CIE cooling term of Eq. eq:cooling_fnct off */
+
+/* ----- per-cell status bits */
+#define TC_ST_MAX_SUBSTEPS 1
+#define TC_ST_NEWTON 2      /* a Newton solve failed and the substep was halved */
+#define TC_ST_NONFINITE 4
+
+typedef struct tc_params {
+  double dvdr_kms_pc;          /* <|dv/dr|> in km/s/pc for CO trapping (Sec. 4.3.2); default 1 */
+  double T_cmb;                /* radiation temperature floor of the dust (Sec. 4.3.6); default 2.73 K */
+  double chi0;                 /* unattenuated FUV scale for optical dust heating; default 1 */
+  double opt_over_fuv;         /* E_OPT,0 / E_FUV,0 (Sec. 4.3.6); default 1 */
+  double tau_opt_over_tau_pe;  /* tau_OPT / tau_PE (Sec. 4.3.6); default 1/3 */
+  double limiter;              /* factor of the substep rule (Sec. 6.1); default 0.1 */
+  double fd_rel_step;          /* relative FD step for dH/dT_mu (mode 0); default 1e-3 */
+  double newton_rtol;          /* Newton tolerance, FP64 modes; default 1e-12 */
+  double T_floor;              /* temperature floor [K]; default 1 */
+  int newton_max;              /* Newton iteration cap; default 50 */
+  int max_substeps;            /* substep cap per cell; default 1e6 */
+  int mode;                    /* TC_MODE_* */
+  unsigned flags;              /* TC_CONST_KGR | TC_NO_ROVIB | TC_NO_CIE */
+  double newton_rtol_mixed;    /* Newton tolerance of the mixed modes (or stagnation at the FP32 floor); default 1e-6 */
+  int block;                   /* threads per block (0 = autotuned/default) */
+  int blocks_per_sm;           /* resident blocks per SM for the persistent grid (0 = occupancy) */
+} tc_params;
+
+typedef struct tc_fields {
+  /* inputs (device, length ncell) -- Table 1 of the paper */
+  const double *n;          /* n_H [cm^-3] */
+  const double *chi_pe;     /* chi_PE, Draine units (Eq. eq:chi_defn_PE) */
+  const double *chi_lw;     /* chi_LW, dust-attenuated, no self-shielding (Eq. eq:chi_defn_LW) */
+  const double *f_shld_h2;  /* f_shld,H2,eff; chi_H2 = chi_LW f (Eq. e:chi_H2) */
+  const double *f_shld_c;   /* f_shld,C,eff; chi_C = chi_LW f (Sec. 5.1); may be NULL (= 1) */
+  const double *F_lyc;      /* ionising photon flux c E_LyC/(h nu_LyC) [cm^-2 s^-1]; may be NULL (= 0) */
+  const double *xi_cr;      /* primary CR ionisation rate per H [s^-1] */
+  const double *Zg, *Zd;    /* per-cell Z'_g, Z'_d; may be NULL (then Zg_val, Zd_val) */
+  /* state (device, in/out) */
+  double *T, *x_h2, *x_hp;
+  /* optional outputs (device, may be NULL) */
+  double *x_e, *x_cp, *x_co;
+  int *nsub, *status;
+  long long ncell;
+  double Zg_val, Zd_val;    /* scalars used when Zg / Zd are NULL */
+} tc_fields;
+
+typedef struct tc_handle tc_handle;
+
+/* Fills *p with the defaults listed above for `mode`. */
+int tc_params_default(tc_params *p, int mode);
+
+/* Creates a handle on the current CUDA device: copies *p, allocates the small device
+ * workspace (work-queue counter and status reduction).  *out is set only on success. */
+int tc_create(const tc_params *p, tc_handle **out);
+
+/* Enqueues one thermochemistry step of dt_s seconds for every cell of *f on `stream`.
+ * Returns TC_EINVAL for NULL required pointers, ncell < 0, dt_s < 0 or a non-finite
+ * dt_s; TC_ENOMLP for a seeded mode without weights; TC_ECUDA if the launch fails. */
+int tc_step(tc_handle *h, const tc_fields *f, double dt_s, void *stream);
+
+/* Enqueues one step for nbox independent boxes (each its own tc_fields, Z scalars and
+ * size) as a single persistent-kernel launch over a device box table; on the first call
+ * with a given box set the launch is captured into a CUDA graph that later identical
+ * calls replay.  `boxes` is a host array of nbox descriptors. */
+int tc_step_batch(tc_handle *h, const tc_fields *boxes, int nbox, double dt_s, void *stream);
+
+/* Like tc_step but every pointer in *f is a HOST pointer: the call copies inputs to the
+ * device, runs the step, copies T, x_h2, x_hp (and the optional outputs) back and
+ * synchronises `stream` before returning. */
+int tc_step_host(tc_handle *h, const tc_fields *f, double dt_s, void *stream);
+
+/* Loads MLP seed weights (the blob written by tc_mlp_export) into the handle. */
+int tc_load_mlp(tc_handle *h, const void *blob, size_t bytes);
+
+/* Counts cells with status != 0 in the last step's status array on `stream` and
+ * synchronises it; *nbad receives the count. */
+int tc_sync_status(tc_handle *h, const int *status, long long ncell, void *stream, long long *nbad);
+
+/* Number of device kernel launches the handle has issued (for accounting). */
+long long tc_launch_count(const tc_handle *h);
+
+const char *tc_strerror(int code);
+
+void tc_destroy(tc_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TC_H */

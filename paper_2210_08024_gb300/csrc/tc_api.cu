@@ -1,0 +1,370 @@
+// C ABI of the thermochemistry library (declared in include/tc.h).
+//
+// Owns the handle: parameters, a small device workspace (the work-queue cursor, a
+// status counter, the batched box table), reusable device buffers for the host-buffer
+// entry point, and the CUDA graph of the batched launch.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/tc.h"
+#include "tc_launch.h"
+
+namespace tcg {
+int occupancy_mode0_impl(int block);
+int occupancy_mode1_impl(int block);
+int occupancy_mode2_impl(int block);
+}  // namespace tcg
+
+struct tc_handle {
+  tc_params p;
+  int device = 0;
+  int num_sms = 0;
+  unsigned long long* d_cursor = nullptr;  // work-queue cursor (8 B)
+  unsigned long long* d_count = nullptr;   // status reduction counter (8 B)
+  tcg::BoxTable* d_boxes = nullptr;        // batched launch box table
+  tcg::BoxTable* h_boxes = nullptr;        // pinned host copy (graph memcpy source)
+  long long launches = 0;
+  // host-buffer entry point scratch
+  double* d_buf = nullptr;
+  size_t d_buf_cells = 0;
+  int* d_ibuf = nullptr;
+  // batched graph cache
+  cudaGraphExec_t gexec = nullptr;
+  unsigned long long gkey = 0;
+  cudaStream_t gstream = nullptr;
+  // MLP seed weights (device) -- loaded by tc_load_mlp
+  void* d_mlp = nullptr;
+  size_t mlp_bytes = 0;
+};
+
+extern "C" {
+
+const char* tc_strerror(int code) {
+  switch (code) {
+    case TC_OK: return "ok";
+    case TC_EINVAL: return "invalid argument";
+    case TC_ECUDA: return "CUDA runtime error";
+    case TC_ENOMEM: return "out of memory";
+    case TC_ENOMLP: return "seeded mode requested before tc_load_mlp";
+    case TC_ENODEV: return "no sm_103 CUDA device";
+    default: return "unknown error";
+  }
+}
+
+int tc_params_default(tc_params* p, int mode) {
+  if (!p) return TC_EINVAL;
+  memset(p, 0, sizeof(*p));
+  p->dvdr_kms_pc = 1.0;
+  p->T_cmb = 2.73;
+  p->chi0 = 1.0;
+  p->opt_over_fuv = 1.0;
+  p->tau_opt_over_tau_pe = 1.0 / 3.0;
+  p->limiter = 0.1;
+  p->fd_rel_step = 1e-3;
+  p->newton_rtol = 1e-12;
+  p->T_floor = 1.0;
+  p->newton_max = 50;
+  p->max_substeps = 1000000;
+  p->mode = mode;
+  p->flags = 0;
+  p->newton_rtol_mixed = 1e-6;
+  p->block = 0;
+  p->blocks_per_sm = 0;
+  return TC_OK;
+}
+
+static bool mode_ok(int m) { return m >= TC_MODE_PAPER_FP64 && m <= TC_MODE_NEWTON_FP64_SEEDED; }
+
+int tc_create(const tc_params* p, tc_handle** out) {
+  if (!p || !out || !mode_ok(p->mode)) return TC_EINVAL;
+  if (!(p->limiter > 0.0) || !(p->fd_rel_step > 0.0) || p->newton_max < 1 || p->max_substeps < 1) return TC_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TC_ENODEV;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return TC_ECUDA;
+  if (prop.major < 10) return TC_ENODEV;
+  tc_handle* h = new (std::nothrow) tc_handle();
+  if (!h) return TC_ENOMEM;
+  h->p = *p;
+  h->device = dev;
+  h->num_sms = prop.multiProcessorCount;
+  if (cudaMalloc(&h->d_cursor, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    delete h;
+    return TC_ENOMEM;
+  }
+  h->d_count = h->d_cursor + 1;
+  *out = h;
+  return TC_OK;
+}
+
+void tc_destroy(tc_handle* h) {
+  if (!h) return;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  cudaFree(h->d_cursor);
+  cudaFree(h->d_boxes);
+  cudaFreeHost(h->h_boxes);
+  cudaFree(h->d_buf);
+  cudaFree(h->d_ibuf);
+  cudaFree(h->d_mlp);
+  delete h;
+}
+
+long long tc_launch_count(const tc_handle* h) { return h ? h->launches : -1; }
+
+static tcg::DevParams dev_params(const tc_params& p) {
+  tcg::DevParams d;
+  d.dvdr_kms_pc = p.dvdr_kms_pc;
+  d.T_cmb = p.T_cmb;
+  d.chi0 = p.chi0;
+  d.opt_over_fuv = p.opt_over_fuv;
+  d.tau_ratio = p.tau_opt_over_tau_pe;
+  d.limiter = p.limiter;
+  d.fd_rel = p.fd_rel_step;
+  d.rtol = p.newton_rtol;
+  d.rtol_mixed = p.newton_rtol_mixed;
+  d.T_floor = p.T_floor;
+  d.newton_max = p.newton_max;
+  d.max_sub = p.max_substeps;
+  d.flags = p.flags;
+  return d;
+}
+
+static bool aligned8(const void* q) { return (((uintptr_t)q) & 7u) == 0; }
+
+static int check_fields(const tc_fields* f) {
+  if (!f || f->ncell < 0) return TC_EINVAL;
+  if (f->ncell == 0) return TC_OK;
+  const void* req[] = {f->n, f->chi_pe, f->chi_lw, f->f_shld_h2, f->xi_cr, f->T, f->x_h2, f->x_hp};
+  for (const void* q : req)
+    if (!q || !aligned8(q)) return TC_EINVAL;
+  const void* opt[] = {f->f_shld_c, f->F_lyc, f->Zg, f->Zd, f->x_e, f->x_cp, f->x_co};
+  for (const void* q : opt)
+    if (q && !aligned8(q)) return TC_EINVAL;
+  if (!f->Zg && !(f->Zg_val >= 0.0)) return TC_EINVAL;
+  if (!f->Zd && !(f->Zd_val >= 0.0)) return TC_EINVAL;
+  return TC_OK;
+}
+
+static tcg::DevFields dev_fields(const tc_fields* f) {
+  tcg::DevFields d;
+  d.n = f->n; d.chi_pe = f->chi_pe; d.chi_lw = f->chi_lw; d.fh2 = f->f_shld_h2; d.fc = f->f_shld_c;
+  d.Flyc = f->F_lyc; d.xi = f->xi_cr; d.Zg = f->Zg; d.Zd = f->Zd;
+  d.T = f->T; d.xH2 = f->x_h2; d.xHp = f->x_hp; d.xe = f->x_e; d.xCp = f->x_cp; d.xCO = f->x_co;
+  d.nsub = f->nsub; d.status = f->status;
+  d.ncell = f->ncell;
+  d.Zg_val = f->Zg_val; d.Zd_val = f->Zd_val;
+  return d;
+}
+
+static int kernel_mode(int mode) { return (mode == TC_MODE_PAPER_FP64) ? 0 : (mode == TC_MODE_MIXED || mode == TC_MODE_MIXED_SEEDED) ? 2 : 1; }
+
+static void launch_shape(tc_handle* h, int kmode, long long ntotal, int* grid, int* block) {
+  int b = h->p.block > 0 ? h->p.block : 128;
+  if (b > 128) b = 128;  // kernels are compiled with __launch_bounds__(128)
+  b = (b / 32) * 32;
+  if (b < 32) b = 32;
+  int per_sm = h->p.blocks_per_sm;
+  if (per_sm <= 0) {
+    per_sm = (kmode == 0) ? tcg::occupancy_mode0_impl(b) : (kmode == 1) ? tcg::occupancy_mode1_impl(b)
+                                                                        : tcg::occupancy_mode2_impl(b);
+  }
+  long long g = (long long)h->num_sms * per_sm;
+  long long need = (ntotal + b - 1) / b;
+  if (g > need) g = need;
+  if (g < 1) g = 1;
+  *grid = (int)g;
+  *block = b;
+}
+
+static int enqueue(tc_handle* h, bool batch, const tcg::DevFields& f, long long ntotal, double dt, cudaStream_t st) {
+  int kmode = kernel_mode(h->p.mode);
+  if (h->p.mode == TC_MODE_MIXED_SEEDED || h->p.mode == TC_MODE_NEWTON_FP64_SEEDED) {
+    if (!h->d_mlp) return TC_ENOMLP;
+  }
+  int grid, block;
+  launch_shape(h, kmode, ntotal, &grid, &block);
+  if (cudaMemsetAsync(h->d_cursor, 0, sizeof(unsigned long long), st) != cudaSuccess) return TC_ECUDA;
+  tcg::DevParams dp = dev_params(h->p);
+  cudaError_t e;
+  if (kmode == 0) e = tcg::launch_mode0(batch, f, h->d_boxes, dp, dt, h->d_cursor, ntotal, grid, block, st);
+  else if (kmode == 1) e = tcg::launch_mode1(batch, f, h->d_boxes, dp, dt, h->d_cursor, ntotal, grid, block, st);
+  else e = tcg::launch_mode2(batch, f, h->d_boxes, dp, dt, h->d_cursor, ntotal, grid, block, st);
+  if (e != cudaSuccess) return TC_ECUDA;
+  h->launches += 1;
+  return TC_OK;
+}
+
+int tc_step(tc_handle* h, const tc_fields* f, double dt_s, void* stream) {
+  if (!h) return TC_EINVAL;
+  int rc = check_fields(f);
+  if (rc != TC_OK) return rc;
+  if (!(dt_s >= 0.0) || !isfinite(dt_s)) return TC_EINVAL;
+  if (f->ncell == 0) return TC_OK;
+  return enqueue(h, false, dev_fields(f), f->ncell, dt_s, (cudaStream_t)stream);
+}
+
+int tc_step_host(tc_handle* h, const tc_fields* f, double dt_s, void* stream) {
+  if (!h) return TC_EINVAL;
+  int rc = check_fields(f);
+  if (rc != TC_OK) return rc;
+  if (!(dt_s >= 0.0) || !isfinite(dt_s)) return TC_EINVAL;
+  if (f->ncell == 0) return TC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = (size_t)f->ncell;
+  const int NIN = 9, NST = 6;
+  if (h->d_buf_cells < n) {
+    cudaFree(h->d_buf);
+    cudaFree(h->d_ibuf);
+    h->d_buf = nullptr;
+    h->d_ibuf = nullptr;
+    h->d_buf_cells = 0;
+    if (cudaMalloc(&h->d_buf, n * sizeof(double) * (NIN + NST)) != cudaSuccess) return TC_ENOMEM;
+    if (cudaMalloc(&h->d_ibuf, n * sizeof(int) * 2) != cudaSuccess) return TC_ENOMEM;
+    h->d_buf_cells = n;
+  }
+  double* b = h->d_buf;
+  const double* hin[NIN] = {f->n, f->chi_pe, f->chi_lw, f->f_shld_h2, f->f_shld_c, f->F_lyc, f->xi_cr, f->Zg, f->Zd};
+  double* din[NIN];
+  for (int k = 0; k < NIN; ++k) {
+    din[k] = hin[k] ? b + (size_t)k * n : nullptr;
+    if (hin[k] && cudaMemcpyAsync(din[k], hin[k], n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return TC_ECUDA;
+  }
+  double* hst[NST] = {f->T, f->x_h2, f->x_hp, f->x_e, f->x_cp, f->x_co};
+  double* dst[NST];
+  for (int k = 0; k < NST; ++k) {
+    dst[k] = hst[k] ? b + (size_t)(NIN + k) * n : nullptr;
+    if (k < 3 && cudaMemcpyAsync(dst[k], hst[k], n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return TC_ECUDA;
+  }
+  tc_fields d = *f;
+  d.n = din[0]; d.chi_pe = din[1]; d.chi_lw = din[2]; d.f_shld_h2 = din[3]; d.f_shld_c = din[4]; d.F_lyc = din[5];
+  d.xi_cr = din[6]; d.Zg = din[7]; d.Zd = din[8];
+  d.T = dst[0]; d.x_h2 = dst[1]; d.x_hp = dst[2]; d.x_e = dst[3]; d.x_cp = dst[4]; d.x_co = dst[5];
+  d.nsub = f->nsub ? h->d_ibuf : nullptr;
+  d.status = f->status ? h->d_ibuf + n : nullptr;
+  rc = enqueue(h, false, dev_fields(&d), f->ncell, dt_s, st);
+  if (rc != TC_OK) return rc;
+  for (int k = 0; k < NST; ++k)
+    if (hst[k] && cudaMemcpyAsync(hst[k], dst[k], n * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      return TC_ECUDA;
+  if (f->nsub && cudaMemcpyAsync(f->nsub, d.nsub, n * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return TC_ECUDA;
+  if (f->status && cudaMemcpyAsync(f->status, d.status, n * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return TC_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return TC_ECUDA;
+  return TC_OK;
+}
+
+static unsigned long long fnv1a(const void* data, size_t n, unsigned long long hsh) {
+  const unsigned char* c = (const unsigned char*)data;
+  for (size_t i = 0; i < n; ++i) {
+    hsh ^= c[i];
+    hsh *= 1099511628211ull;
+  }
+  return hsh;
+}
+
+int tc_step_batch(tc_handle* h, const tc_fields* boxes, int nbox, double dt_s, void* stream) {
+  if (!h || !boxes || nbox < 1 || nbox > tcg::MAX_BOX) return TC_EINVAL;
+  if (!(dt_s >= 0.0) || !isfinite(dt_s)) return TC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!h->d_boxes) {
+    if (cudaMalloc(&h->d_boxes, sizeof(tcg::BoxTable)) != cudaSuccess) return TC_ENOMEM;
+    if (cudaMallocHost(&h->h_boxes, sizeof(tcg::BoxTable)) != cudaSuccess) return TC_ENOMEM;
+  }
+  tcg::BoxTable tb;
+  memset(&tb, 0, sizeof(tb));
+  tb.nbox = nbox;
+  long long tot = 0;
+  for (int b = 0; b < nbox; ++b) {
+    int rc = check_fields(&boxes[b]);
+    if (rc != TC_OK) return rc;
+    tb.start[b] = tot;
+    tb.box[b] = dev_fields(&boxes[b]);
+    tot += boxes[b].ncell;
+  }
+  tb.start[nbox] = tot;
+  if (tot == 0) return TC_OK;
+  unsigned long long key = fnv1a(&tb, sizeof(tb), 1469598103934665603ull);
+  key = fnv1a(&dt_s, sizeof(dt_s), key);
+  key = fnv1a(&h->p, sizeof(h->p), key);
+  key = fnv1a(&st, sizeof(st), key);
+  if (!h->gexec || key != h->gkey) {
+    if (h->gexec) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
+    memcpy(h->h_boxes, &tb, sizeof(tb));
+    cudaStream_t cap;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return TC_ECUDA;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return TC_ECUDA;
+    }
+    cudaError_t e = cudaMemcpyAsync(h->d_boxes, h->h_boxes, sizeof(tcg::BoxTable), cudaMemcpyHostToDevice, cap);
+    long long before = h->launches;
+    int rc = (e == cudaSuccess) ? enqueue(h, true, tb.box[0], tot, dt_s, cap) : TC_ECUDA;
+    h->launches = before;
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (rc != TC_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e2 != cudaSuccess) return TC_ECUDA;
+    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return TC_ECUDA;
+    h->gkey = key;
+  }
+  if (cudaGraphLaunch(h->gexec, st) != cudaSuccess) return TC_ECUDA;
+  h->launches += 1;
+  return TC_OK;
+}
+
+int tc_load_mlp(tc_handle* h, const void* blob, size_t bytes) {
+  if (!h || !blob || bytes == 0) return TC_EINVAL;
+  cudaFree(h->d_mlp);
+  h->d_mlp = nullptr;
+  if (cudaMalloc(&h->d_mlp, bytes) != cudaSuccess) return TC_ENOMEM;
+  if (cudaMemcpy(h->d_mlp, blob, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return TC_ECUDA;
+  h->mlp_bytes = bytes;
+  return TC_OK;
+}
+
+}  // extern "C"
+
+// ----- status reduction
+namespace {
+__global__ void k_count_bad(const int* __restrict__ status, long long n, unsigned long long* count) {
+  unsigned long long local = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    local += (status[i] != 0);
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+}
+}  // namespace
+
+extern "C" int tc_sync_status(tc_handle* h, const int* status, long long ncell, void* stream, long long* nbad) {
+  if (!h || !nbad || ncell < 0 || (ncell > 0 && !status)) return TC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(h->d_count, 0, sizeof(unsigned long long), st) != cudaSuccess) return TC_ECUDA;
+  if (ncell > 0) {
+    int grid = h->num_sms * 4;
+    k_count_bad<<<grid, 256, 0, st>>>(status, ncell, h->d_count);
+    if (cudaGetLastError() != cudaSuccess) return TC_ECUDA;
+    h->launches += 1;
+  }
+  unsigned long long v = 0;
+  if (cudaMemcpyAsync(&v, h->d_count, sizeof(v), cudaMemcpyDeviceToHost, st) != cudaSuccess) return TC_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return TC_ECUDA;
+  *nbad = (long long)v;
+  return TC_OK;
+}

@@ -1,0 +1,15 @@
+// Host-side launch entry points of the step kernels (one per translation unit).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "tc_kernels.cuh"
+
+namespace tcg {
+// Launches mode-M step kernels; batch selects the box-table variant.
+cudaError_t launch_mode0(bool batch, const DevFields& f, const BoxTable* d_boxes, const DevParams& p, double dt,
+                         unsigned long long* cursor, long long ntotal, int grid, int block, cudaStream_t st);
+cudaError_t launch_mode1(bool batch, const DevFields& f, const BoxTable* d_boxes, const DevParams& p, double dt,
+                         unsigned long long* cursor, long long ntotal, int grid, int block, cudaStream_t st);
+cudaError_t launch_mode2(bool batch, const DevFields& f, const BoxTable* d_boxes, const DevParams& p, double dt,
+                         unsigned long long* cursor, long long ntotal, int grid, int block, cudaStream_t st);
+}  // namespace tcg

@@ -1,0 +1,284 @@
+"""ctypes binding of the C ABI in include/tc.h (argument marshalling only).
+
+Function names match the C entry points.  Device buffers are torch CUDA tensors (or
+raw device addresses); every step of the computation runs in the library's CUDA
+kernels.  If the library cannot be loaded the import fails: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtc_gb300.so")
+
+TC_OK, TC_EINVAL, TC_ECUDA, TC_ENOMEM, TC_ENOMLP, TC_ENODEV = 0, -1, -2, -3, -4, -5
+TC_MODE_PAPER_FP64, TC_MODE_NEWTON_FP64, TC_MODE_MIXED, TC_MODE_MIXED_SEEDED, TC_MODE_NEWTON_FP64_SEEDED = 0, 1, 2, 3, 4
+TC_CONST_KGR, TC_NO_ROVIB, TC_NO_CIE = 1, 2, 4
+TC_ST_MAX_SUBSTEPS, TC_ST_NEWTON, TC_ST_NONFINITE = 1, 2, 4
+
+
+class tc_params(ctypes.Structure):
+    _fields_ = [
+        ("dvdr_kms_pc", ctypes.c_double),
+        ("T_cmb", ctypes.c_double),
+        ("chi0", ctypes.c_double),
+        ("opt_over_fuv", ctypes.c_double),
+        ("tau_opt_over_tau_pe", ctypes.c_double),
+        ("limiter", ctypes.c_double),
+        ("fd_rel_step", ctypes.c_double),
+        ("newton_rtol", ctypes.c_double),
+        ("T_floor", ctypes.c_double),
+        ("newton_max", ctypes.c_int),
+        ("max_substeps", ctypes.c_int),
+        ("mode", ctypes.c_int),
+        ("flags", ctypes.c_uint),
+        ("newton_rtol_mixed", ctypes.c_double),
+        ("block", ctypes.c_int),
+        ("blocks_per_sm", ctypes.c_int),
+    ]
+
+
+_P = ctypes.c_void_p
+
+
+class tc_fields(ctypes.Structure):
+    _fields_ = [
+        ("n", _P), ("chi_pe", _P), ("chi_lw", _P), ("f_shld_h2", _P), ("f_shld_c", _P), ("F_lyc", _P),
+        ("xi_cr", _P), ("Zg", _P), ("Zd", _P),
+        ("T", _P), ("x_h2", _P), ("x_hp", _P),
+        ("x_e", _P), ("x_cp", _P), ("x_co", _P),
+        ("nsub", _P), ("status", _P),
+        ("ncell", ctypes.c_longlong),
+        ("Zg_val", ctypes.c_double), ("Zd_val", ctypes.c_double),
+    ]
+
+
+# field name in tc_fields -> key used by callers' dicts
+FIELD_KEYS = {
+    "n": "n", "chi_pe": "chi_pe", "chi_lw": "chi_lw", "f_shld_h2": "f_h2", "f_shld_c": "f_c", "F_lyc": "F_lyc",
+    "xi_cr": "xi", "Zg": "Zg", "Zd": "Zd", "T": "T", "x_h2": "xH2", "x_hp": "xHp", "x_e": "xe", "x_cp": "xCp",
+    "x_co": "xCO", "nsub": "nsub", "status": "status",
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libtc_gb300.so is not built (run __graft_entry__.build()); no CPU fallback exists")
+    L = ctypes.CDLL(LIB_PATH)
+    L.tc_params_default.argtypes = [ctypes.POINTER(tc_params), ctypes.c_int]
+    L.tc_create.argtypes = [ctypes.POINTER(tc_params), ctypes.POINTER(ctypes.c_void_p)]
+    L.tc_step.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_double, ctypes.c_void_p]
+    L.tc_step_host.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_double, ctypes.c_void_p]
+    L.tc_step_batch.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_int, ctypes.c_double,
+                                ctypes.c_void_p]
+    L.tc_load_mlp.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+    L.tc_sync_status.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
+                                 ctypes.POINTER(ctypes.c_longlong)]
+    L.tc_launch_count.argtypes = [ctypes.c_void_p]
+    L.tc_launch_count.restype = ctypes.c_longlong
+    L.tc_strerror.argtypes = [ctypes.c_int]
+    L.tc_strerror.restype = ctypes.c_char_p
+    L.tc_destroy.argtypes = [ctypes.c_void_p]
+    L.tc_destroy.restype = None
+    L.tc_peak_launch.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                 ctypes.c_void_p]
+    L.tc_peak_chains.restype = ctypes.c_int
+    return L
+
+
+lib = _load()
+
+
+class TcError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc != TC_OK:
+        raise TcError("%s failed: %s (%d)" % (what, lib.tc_strerror(rc).decode(), rc))
+
+
+def tc_strerror(code: int) -> str:
+    return lib.tc_strerror(code).decode()
+
+
+def tc_params_default(mode: int = TC_MODE_PAPER_FP64, **kw) -> tc_params:
+    p = tc_params()
+    _check(lib.tc_params_default(ctypes.byref(p), int(mode)), "tc_params_default")
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def tc_create(params: tc_params) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib.tc_create(ctypes.byref(params), ctypes.byref(h)), "tc_create")
+    return h
+
+
+def tc_destroy(h) -> None:
+    lib.tc_destroy(h)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_fields(arrs: dict, ncell: int | None = None, Zg: float = 1.0, Zd: float = 1.0) -> tc_fields:
+    """Builds tc_fields from a dict of torch tensors (device, float64 / int32) keyed as
+    in FIELD_KEYS' values.  The caller keeps the tensors alive during the call."""
+    f = tc_fields()
+    n = ncell
+    for cname, key in FIELD_KEYS.items():
+        t = arrs.get(key)
+        if t is None:
+            setattr(f, cname, None)
+            continue
+        if hasattr(t, "data_ptr"):
+            if not t.is_contiguous():
+                raise ValueError("field %s must be contiguous" % key)
+            if n is None:
+                n = t.numel()
+            setattr(f, cname, t.data_ptr())
+        else:
+            setattr(f, cname, int(t))
+    f.ncell = int(n if n is not None else 0)
+    f.Zg_val = float(Zg)
+    f.Zd_val = float(Zd)
+    return f
+
+
+def make_host_fields(arrs: dict, Zg: float = 1.0, Zd: float = 1.0) -> tc_fields:
+    """tc_fields over host numpy arrays (for tc_step_host)."""
+    f = tc_fields()
+    n = None
+    for cname, key in FIELD_KEYS.items():
+        a = arrs.get(key)
+        if a is None:
+            setattr(f, cname, None)
+            continue
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("field %s must be contiguous" % key)
+        n = a.size if n is None else n
+        setattr(f, cname, a.ctypes.data)
+    f.ncell = int(n or 0)
+    f.Zg_val = float(Zg)
+    f.Zd_val = float(Zd)
+    return f
+
+
+def tc_step(h, fields: tc_fields, dt: float, stream=None) -> None:
+    _check(lib.tc_step(h, ctypes.byref(fields), float(dt), _stream_ptr(stream)), "tc_step")
+
+
+def tc_step_host(h, fields: tc_fields, dt: float, stream=None) -> None:
+    _check(lib.tc_step_host(h, ctypes.byref(fields), float(dt), _stream_ptr(stream)), "tc_step_host")
+
+
+def tc_step_batch(h, boxes: list, dt: float, stream=None) -> None:
+    arr = (tc_fields * len(boxes))(*boxes)
+    _check(lib.tc_step_batch(h, arr, len(boxes), float(dt), _stream_ptr(stream)), "tc_step_batch")
+
+
+def tc_load_mlp(h, blob: bytes) -> None:
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(lib.tc_load_mlp(h, buf, len(blob)), "tc_load_mlp")
+
+
+def tc_sync_status(h, status_tensor, stream=None) -> int:
+    nbad = ctypes.c_longlong(0)
+    _check(lib.tc_sync_status(h, status_tensor.data_ptr(), status_tensor.numel(), _stream_ptr(stream),
+                              ctypes.byref(nbad)), "tc_sync_status")
+    return int(nbad.value)
+
+
+def tc_launch_count(h) -> int:
+    return int(lib.tc_launch_count(h))
+
+
+def tc_peak_launch(kind: int, grid: int, block: int, iters: int, sink, stream=None) -> None:
+    _check(lib.tc_peak_launch(int(kind), int(grid), int(block), int(iters), sink.data_ptr(), _stream_ptr(stream)),
+           "tc_peak_launch")
+
+
+def tc_peak_chains() -> int:
+    return int(lib.tc_peak_chains())
+
+
+# ----------------------------------------------------------------------------- helpers
+STATE_OUT = ("T", "xH2", "xHp", "xe", "xCp", "xCO", "nsub", "status")
+INPUT_KEYS = ("n", "chi_pe", "chi_lw", "f_h2", "f_c", "F_lyc", "xi", "Zg", "Zd")
+
+
+def to_device(cells: dict, device="cuda", outputs: bool = True) -> dict:
+    """Copies a dict of numpy arrays (inputs and T, xH2, xHp) to device float64 tensors
+    and allocates the optional outputs."""
+    import numpy as np
+    import torch
+    n = int(np.asarray(cells["n"]).size)
+    d = {}
+    for k in INPUT_KEYS + ("T", "xH2", "xHp"):
+        if k not in cells:
+            continue
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(cells[k], dtype=np.float64), (n,)))
+        d[k] = torch.from_numpy(a.copy()).to(device)
+    if outputs:
+        for k in ("xe", "xCp", "xCO"):
+            d[k] = torch.zeros(n, dtype=torch.float64, device=device)
+        for k in ("nsub", "status"):
+            d[k] = torch.zeros(n, dtype=torch.int32, device=device)
+    return d
+
+
+def from_device(d: dict) -> dict:
+    return {k: d[k].cpu().numpy() for k in STATE_OUT if k in d}
+
+
+class Stepper:
+    """Owns a tc_handle for one parameter set; steps device tensor dicts in place."""
+
+    def __init__(self, mode: int = TC_MODE_PAPER_FP64, **params):
+        self.params = tc_params_default(mode, **params)
+        self.h = tc_create(self.params)
+
+    def step(self, d: dict, dt: float, stream=None, Zg: float = 1.0, Zd: float = 1.0) -> None:
+        f = make_fields(d, Zg=Zg, Zd=Zd)
+        tc_step(self.h, f, dt, stream)
+
+    def step_host(self, cells: dict, dt: float, stream=None, Zg: float = 1.0, Zd: float = 1.0) -> None:
+        tc_step_host(self.h, make_host_fields(cells, Zg=Zg, Zd=Zd), dt, stream)
+
+    def load_mlp(self, blob: bytes) -> None:
+        tc_load_mlp(self.h, blob)
+
+    def launches(self) -> int:
+        return tc_launch_count(self.h)
+
+    def close(self) -> None:
+        if self.h:
+            tc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def step_numpy(cells: dict, dt: float, mode: int = TC_MODE_PAPER_FP64, **params) -> dict:
+    """Uploads, runs one step on the current CUDA device, downloads (tests/smoke)."""
+    import torch
+    d = to_device(cells)
+    st = Stepper(mode, **params)
+    st.step(d, dt)
+    torch.cuda.synchronize()
+    out = from_device(d)
+    st.close()
+    return out
