@@ -724,7 +724,7 @@ template <class R> inline bool solve3(R J[3][3], R b[3], R d[3]) {
 
 // One backward-Euler substep y - y^n - dt f(y) = 0 by Newton's method with a forward-
 // difference Jacobian (relative step 1e-7; abundance steps floored at 1e-17) and
-// fraction-to-boundary damping that keeps T_mu, x_H2, x_H+ and x_H positive.  Converged
+// damping that keeps T_mu, x_H2, x_H+ and x_H positive (see below).  Converged
 // when every full (undamped) step satisfies |d_i| <= rtol |y_i| (READING: relative for
 // every component, so abundances as small as 1e-25 are still converged relatively).
 // Returns the iteration count, or -1 on failure.
@@ -747,23 +747,46 @@ template <class R> int newton_substep(const CellIn& c, const Params& p, const Pr
     for (int i = 0; i < 3; ++i) rhs[i] = R(0.0) - (y[i] - yn[i] - dts * f[i]);
     R d[3];
     if (!solve3(J, rhs, d)) return -1;
-    R lam = R(1.0);
-    for (int i = 0; i < 3; ++i) {
-      if (d[i] < R(0.0)) {
+    // Damping (READING; the root is unchanged, only the path to it), by blocks:
+    //  - T_mu takes the step length lamT that keeps it at >= 1% of its value;
+    //  - x_H2 and x_H+ share a step length lamX that keeps them and
+    //    x_H = 1 - 2 x_H2 - x_H+ at >= 1% of their values (fraction 0.99 to the
+    //    boundary), so that an abundance pressed against its bound does not freeze
+    //    the temperature, nor the temperature the abundances;
+    //  - an abundance whose step is below 1e-8 in absolute terms cannot matter to the
+    //    other unknowns: it does not limit lamX and is kept at >= 1% of its value on
+    //    its own, so that a trace species driven towards zero does not freeze the rest.
+    // Converged when no limit acted and every step is below newton_rtol |y_i|.
+    R lamT = R(1.0);
+    if (d[0] < R(0.0)) {
+      R cap = R(0.99) * y[0] / (R(0.0) - d[0]);
+      if (cap < lamT) lamT = cap;
+    }
+    R lamX = R(1.0);
+    bool tiny[3] = {false, false, false};
+    for (int i = 1; i < 3; ++i) {
+      tiny[i] = !(rabs(d[i]) > R(1e-8));
+      if (d[i] < R(0.0) && !tiny[i]) {
         R cap = R(0.99) * y[i] / (R(0.0) - d[i]);
-        if (cap < lam) lam = cap;
+        if (cap < lamX) lamX = cap;
       }
     }
     R xH = R(1.0) - R(2.0) * y[1] - y[2];
     R dxH = R(0.0) - R(2.0) * d[1] - d[2];
     if (dxH < R(0.0)) {
       R cap = R(0.99) * rmax(xH, R(0.0)) / (R(0.0) - dxH);
-      if (cap < lam) lam = cap;
+      if (cap < lamX) lamX = cap;
     }
-    bool conv = !(lam < R(1.0));
+    bool conv = !(lamT < R(1.0)) && !(lamX < R(1.0));
     for (int i = 0; i < 3; ++i) {
-      R step = lam * d[i];
-      y[i] = y[i] + step;
+      R st = ((i == 0) ? lamT : lamX) * d[i];
+      if (tiny[i] && y[i] + st < R(0.01) * y[i]) {
+        st = R(0.0) - R(0.99) * y[i];
+        conv = false;
+      }
+      R yi = y[i] + st;
+      R step = yi - y[i];
+      y[i] = yi;
       R tol = R(p.newton_rtol) * rabs(y[i]) + R(1e-300);
       if (rabs(step) > tol) conv = false;
     }
