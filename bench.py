@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--side", type=int, default=128)
-    ap.add_argument("--modes", default="newton,paper", help="comma list of modes to time (first = headline)")
+    ap.add_argument("--modes", default="newton,mixed,paper", help="comma list of modes to time (first = headline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-peaks", action="store_true", help="skip the pipe microbenchmarks (no roofline)")
@@ -302,6 +302,8 @@ def report(args, results, head, ncell, peaks, e2e, clocks, cells, ws):
                       "mode": head, "cells_per_gpu": ncell, "l2": "inputs larger than L2 (%.0f MB)" %
                       (ncell * 13 * 8 / 1e6), "parallelism": "dp%d (independent cells)" % ws},
            "modes": {k: {kk: vv for kk, vv in v.items() if kk != "mode_id"} for k, v in results.items()},
+           "speedup_vs_plain_fp64": {k: v["value"] / results["newton"]["value"] for k, v in results.items()
+                                     if "newton" in results},
            "gpu_launches": r["launches"], "e2e": e2e, "roofline": roofline, "clocks": clocks,
            "peaks": None if peaks is None else {
                "fp64_tflops": 2.0 * peaks["fp64_fma_per_s"] / 1e12,

@@ -41,7 +41,8 @@ extern "C" {
 /* ----- integration modes */
 #define TC_MODE_PAPER_FP64 0   /* the paper's sequential update (Sec. 6.1), FP64 throughout */
 #define TC_MODE_NEWTON_FP64 1  /* coupled backward Euler on (T_mu, x_H2, x_H+) by Newton, FP64 */
-#define TC_MODE_MIXED 2        /* as TC_MODE_NEWTON_FP64, source terms in FP32, Newton in FP64 */
+#define TC_MODE_MIXED 2        /* as TC_MODE_NEWTON_FP64: Newton iterations on FP32 source terms, FP64 residual,
+                                  update, closure x_H, substep length and a final FP64 polish of each root */
 #define TC_MODE_MIXED_SEEDED 3 /* as TC_MODE_MIXED, each Newton solve seeded by the MLP */
 #define TC_MODE_NEWTON_FP64_SEEDED 4 /* as TC_MODE_NEWTON_FP64, MLP-seeded */
 
@@ -50,10 +51,14 @@ extern "C" {
 #define TC_NO_ROVIB 2u   /* H2 ro-vibrational cooling off (Sec. 7.1.2 comparison) */
 #define TC_NO_CIE 4u     /* He + metal CIE cooling term of Eq. eq:cooling_fnct off */
 
-/* ----- per-cell status bits */
+/* ----- per-cell status bits.  Bits 1, 2 and 4 mark numerical trouble (tc_sync_status
+ * counts cells with any of them); bits 8 and 16 are informational (mixed modes). */
 #define TC_ST_MAX_SUBSTEPS 1
-#define TC_ST_NEWTON 2      /* a Newton solve failed and the substep was halved */
+#define TC_ST_NEWTON 2       /* a Newton solve failed and the substep was halved */
 #define TC_ST_NONFINITE 4
+#define TC_ST_FALLBACK 8     /* a mixed solve did not converge; the FP64 Newton finished that substep */
+#define TC_ST_POLISHED 16    /* a mixed solve stopped at the FP32 rounding floor before its FP64 polish */
+#define TC_ST_ERROR_MASK 7
 
 typedef struct tc_params {
   double dvdr_kms_pc;          /* <|dv/dr|> in km/s/pc for CO trapping (Sec. 4.3.2); default 1 */
@@ -69,7 +74,7 @@ typedef struct tc_params {
   int max_substeps;            /* substep cap per cell; default 1e6 */
   int mode;                    /* TC_MODE_* */
   unsigned flags;              /* TC_CONST_KGR | TC_NO_ROVIB | TC_NO_CIE */
-  double newton_rtol_mixed;    /* Newton tolerance of the mixed modes (or stagnation at the FP32 floor); default 1e-6 */
+  double newton_rtol_mixed;    /* step tolerance of the FP32 Newton iterations of the mixed modes; default 1e-7 */
   int block;                   /* threads per block (0 = autotuned/default) */
   int blocks_per_sm;           /* resident blocks per SM for the persistent grid (0 = occupancy) */
 } tc_params;
@@ -121,8 +126,8 @@ int tc_step_host(tc_handle *h, const tc_fields *f, double dt_s, void *stream);
 /* Loads MLP seed weights (the blob written by tc_mlp_export) into the handle. */
 int tc_load_mlp(tc_handle *h, const void *blob, size_t bytes);
 
-/* Counts cells with status != 0 in the last step's status array on `stream` and
- * synchronises it; *nbad receives the count. */
+/* Counts cells whose status has any TC_ST_ERROR_MASK bit in the last step's status array
+ * on `stream` and synchronises it; *nbad receives the count. */
 int tc_sync_status(tc_handle *h, const int *status, long long ncell, void *stream, long long *nbad);
 
 /* Number of device kernel launches the handle has issued (for accounting). */

@@ -72,7 +72,7 @@ int tc_params_default(tc_params* p, int mode) {
   p->max_substeps = 1000000;
   p->mode = mode;
   p->flags = 0;
-  p->newton_rtol_mixed = 1e-6;
+  p->newton_rtol_mixed = 1e-7;
   p->block = 0;
   p->blocks_per_sm = 0;
   return TC_OK;
@@ -346,7 +346,7 @@ namespace {
 __global__ void k_count_bad(const int* __restrict__ status, long long n, unsigned long long* count) {
   unsigned long long local = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    local += (status[i] != 0);
+    local += ((status[i] & TC_ST_ERROR_MASK) != 0);
   for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
   if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
 }

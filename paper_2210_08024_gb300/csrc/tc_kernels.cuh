@@ -9,7 +9,10 @@
 //
 // MODE 0: the paper's sequential update (Sec. 6.1), FP64.
 // MODE 1: coupled backward Euler on (T_mu, x_H2, x_H+) by Newton, FP64.
-// MODE 2: as 1 with the source terms in FP32 and the Newton update in FP64.
+// MODE 2: as 1 with the rates, the C/O/e equilibrium and the heating/cooling sums in
+//         FP32, and the Newton update, its residual and the closure
+//         x_H = 1 - 2 x_H2 - x_H+ in FP64; a substep whose mixed solve does not
+//         converge is re-solved by the FP64 Newton of mode 1 on the same substep.
 #pragma once
 #include <type_traits>
 
@@ -33,7 +36,7 @@ struct BoxTable {
   DevFields box[MAX_BOX];
 };
 
-constexpr int ST_MAX_SUB = 1, ST_NEWTON = 2, ST_NONFIN = 4;
+constexpr int ST_MAX_SUB = 1, ST_NEWTON = 2, ST_NONFIN = 4, ST_FALLBACK = 8, ST_POLISH = 16;
 
 __device__ __forceinline__ long long claim_cells(unsigned long long* cursor) {
   unsigned mask = __activemask();
@@ -113,7 +116,7 @@ TCG_FN void substep_paper(const CellC<double>& c, const DevParams& p, double dt,
     q.xOp = c.xOtot * s.xHp;
     q.xC = c.xCtot - s.xCp - s.xCO;
     q.xO = c.xOtot - s.xCO - q.xOp;
-    Src<double> sr = source(c, b, k, s.xH2, s.xHp, q, Tdf, s.Td);
+    Src<double> sr = source(c, b, k, s.xH2, s.xHp, 1.0 - 2.0 * s.xH2 - s.xHp, q, Tdf, s.Td);
     if (pass == 0) { H0 = sr.H; CH2 = sr.CH2; CHp = sr.CHp; Td0 = sr.Td; }
     else Hp = sr.H;
   }
@@ -135,7 +138,7 @@ TCG_FN void substep_paper(const CellC<double>& c, const DevParams& p, double dt,
   // abundances: 2x2 backward Euler with rates at T^{n+1} = mu^n T_mu^{n+1}, x^n, x_e^n
   const double T1 = s.mu * Tmu_new;
   ChemT<double> b1 = chem_T(c, T1, p.flags);
-  HRate<double> r = h_rates(c, b1, s.xH2, s.xHp, s.xe, log_psi(c, b1, s.xe));
+  HRate<double> r = h_rates(c, b1, s.xH2, 1.0 - 2.0 * s.xH2 - s.xHp, s.xe, log_psi(c, b1, s.xe));
   // (I - A dts) X' = X + b dts in closed form, expanded so that every term is
   // non-negative: a = 2 k_gr n + D_H2 and c = I + R are the diagonal loss rates.
   const double a = 2.0 * r.kn + r.DH2;
@@ -153,18 +156,17 @@ TCG_FN void substep_paper(const CellC<double>& c, const DevParams& p, double dt,
   s.t = last ? dt : s.t + dts;
 }
 
-// ------------------------------------------------------------------ modes 1/2: coupled Newton
+// ------------------------------------------------------------------ mode 1: coupled Newton, FP64
 // f(y) = (H/K, C_H2, C_H+) at T = mu^n y0 with the C/O/e equilibrium and T_d re-solved.
-template <class F> TCG_FN void feval(const CellC<F>& c, const ChemT<F>& b, const CoolT<F>& k,
-                                                         double y1, double y2, double Kinv, F& xe_guess, F& td_guess,
-                                                         double* f) {
-  Equil<F> q = equilibrium(c, b, F(y1), F(y2), xe_guess);
-  Src<F> s = source(c, b, k, F(y1), F(y2), q, F(-1), td_guess);
+TCG_FN void feval64(const CellC<double>& c, const ChemT<double>& b, const CoolT<double>& k, double y1,
+                    double y2, double Kinv, double& xe_guess, double& td_guess, double* f) {
+  Equil<double> q = equilibrium(c, b, y1, y2, xe_guess);
+  Src<double> s = source(c, b, k, y1, y2, 1.0 - 2.0 * y1 - y2, q, -1.0, td_guess);
   xe_guess = q.xe;
   td_guess = s.Td;
-  f[0] = double(s.H) * Kinv;
-  f[1] = double(s.CH2);
-  f[2] = double(s.CHp);
+  f[0] = s.H * Kinv;
+  f[1] = s.CH2;
+  f[2] = s.CHp;
 }
 
 TCG_FN bool solve3(double J[3][3], double b[3], double d[3]) {
@@ -194,103 +196,130 @@ TCG_FN bool solve3(double J[3][3], double b[3], double d[3]) {
   return true;
 }
 
-// One Newton solve of y - y^n - dts f(y) = 0 from `y` (seed on entry, root on exit).
+// Damping of a Newton step d, by blocks (the root is unchanged, only the path to it):
+// T_mu takes the step length lamT that keeps it at >= 1% of its value; x_H2 and x_H+
+// share a length lamX that keeps them and x_H = 1 - 2 x_H2 - x_H+ at >= 1% of their
+// values (fraction 0.99 to the boundary), so that neither block freezes the other.  An
+// abundance whose step is below 1e-8 in absolute terms does not limit lamX and is kept
+// at >= 1% of its value on its own.  Applies the step to y, writes the steps taken to
+// st and returns true if no limit acted (a full Newton step).
+TCG_FN bool damped_step(double* y, const double* d, double* st) {
+  double lamT = 1.0, lamX = 1.0;
+  if (d[0] < 0.0) lamT = fmin(lamT, 0.99 * y[0] / (-d[0]));
+  bool tiny[3] = {false, false, false};
+  for (int i = 1; i < 3; ++i) {
+    tiny[i] = !(fabs(d[i]) > 1e-8);
+    if (d[i] < 0.0 && !tiny[i]) lamX = fmin(lamX, 0.99 * y[i] / (-d[i]));
+  }
+  const double xH = 1.0 - 2.0 * y[1] - y[2];
+  const double dxH = -2.0 * d[1] - d[2];
+  if (dxH < 0.0) lamX = fmin(lamX, 0.99 * fmax(xH, 0.0) / (-dxH));
+  bool full = !(lamT < 1.0) && !(lamX < 1.0);
+  for (int i = 0; i < 3; ++i) {
+    double s = ((i == 0) ? lamT : lamX) * d[i];
+    if (tiny[i] && y[i] + s < 0.01 * y[i]) {
+      s = -0.99 * y[i];
+      full = false;
+    }
+    const double yi = y[i] + s;
+    st[i] = yi - y[i];
+    y[i] = yi;
+  }
+  return full;
+}
+
+// One Newton solve of y - y^n - dts f(y) = 0 from `y` (seed on entry, root on exit),
+// forward-difference Jacobian every iteration (relative step 1e-7, abundance steps
+// floored at 1e-17), converged when every full step is below rtol |y_i|.
 // Returns iterations used, or -1.
-template <class F> TCG_FN int newton_solve(const CellC<F>& c, const DevParams& p, double mu,
-                                                               double Kinv, const double* yn, double dts, double* y,
-                                                               F& xe_g, F& td_g) {
-  const bool fp32 = sizeof(F) == 4;
-  const double rtol = fp32 ? p.rtol_mixed : p.rtol;
-  const double hrel = fp32 ? 3e-4 : 1e-7;
-  const double hfloor = fp32 ? 1e-12 : 1e-17;
-  double prev_rel = 1e300;
+TCG_FN int newton_solve(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
+                        double dts, double* y, double& xe_g, double& td_g) {
   for (int it = 1; it <= p.newton_max; ++it) {
     double f0[3], J[3][3];
-    ChemT<F> b = chem_T(c, F(mu * y[0]), p.flags);
-    CoolT<F> k = cool_T(c, b, p.flags);
+    ChemT<double> b = chem_T(c, mu * y[0], p.flags);
+    CoolT<double> k = cool_T(c, b, p.flags);
     // evaluation order: x_H2 column, x_H+ column, base point (all at the base T), then
     // the T_mu column, so the temperature blocks are built twice per iteration.
     double fx[2][3];
 #pragma unroll 1
     for (int j = 1; j < 3; ++j) {
-      double h = fmax(hrel * fabs(y[j]), hfloor);
+      double h = fmax(1e-7 * fabs(y[j]), 1e-17);
       double y1 = y[1] + ((j == 1) ? h : 0.0), y2 = y[2] + ((j == 2) ? h : 0.0);
-      F xg = xe_g, tg = td_g;
-      feval<F>(c, b, k, y1, y2, Kinv, xg, tg, fx[j - 1]);
+      double xg = xe_g, tg = td_g;
+      feval64(c, b, k, y1, y2, Kinv, xg, tg, fx[j - 1]);
     }
-    feval<F>(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0);
+    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0);
     for (int j = 1; j < 3; ++j) {
-      double h = fmax(hrel * fabs(y[j]), hfloor);
+      double h = fmax(1e-7 * fabs(y[j]), 1e-17);
       for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - dts * (fx[j - 1][i] - f0[i]) / h;
     }
     {
-      double h = hrel * y[0];
-      ChemT<F> bT = chem_T(c, F(mu * (y[0] + h)), p.flags);
-      CoolT<F> kT = cool_T(c, bT, p.flags);
-      F xg = xe_g, tg = td_g;
+      double h = 1e-7 * y[0];
+      ChemT<double> bT = chem_T(c, mu * (y[0] + h), p.flags);
+      CoolT<double> kT = cool_T(c, bT, p.flags);
+      double xg = xe_g, tg = td_g;
       double fT[3];
-      feval<F>(c, bT, kT, y[1], y[2], Kinv, xg, tg, fT);
+      feval64(c, bT, kT, y[1], y[2], Kinv, xg, tg, fT);
       for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - dts * (fT[i] - f0[i]) / h;
     }
     double rhs[3], d[3];
     for (int i = 0; i < 3; ++i) rhs[i] = -(y[i] - yn[i] - dts * f0[i]);
     if (!solve3(J, rhs, d)) return -1;
-    double lam = 1.0;
+    double st[3];
+    bool conv = damped_step(y, d, st);
     for (int i = 0; i < 3; ++i)
-      if (d[i] < 0.0) lam = fmin(lam, 0.99 * y[i] / (-d[i]));
-    const double xH = 1.0 - 2.0 * y[1] - y[2];
-    const double dxH = -2.0 * d[1] - d[2];
-    if (dxH < 0.0) lam = fmin(lam, 0.99 * fmax(xH, 0.0) / (-dxH));
-    bool conv = !(lam < 1.0);
-    double relmax = 0.0;
-    for (int i = 0; i < 3; ++i) {
-      const double st = lam * d[i];
-      y[i] += st;
-      if (fp32) {
-        // FP32 source terms put a rounding floor under the step: measure abundances
-        // against 1e-10 (the mixed accuracy target is absolute) and stop either at the
-        // tolerance or once the step stagnates at the floor.
-        relmax = fmax(relmax, fabs(st) / fmax(fabs(y[i]), (i == 0) ? 0.0 : 1e-10));
-      } else {
-        const double tol = rtol * fabs(y[i]) + 1e-300;
-        if (fabs(st) > tol) conv = false;
-      }
-    }
+      if (fabs(st[i]) > p.rtol * fabs(y[i]) + 1e-300) conv = false;
     if (!finite3(y[0], y[1], y[2])) return -1;
-    if (fp32) {
-      conv = conv && (relmax <= rtol || (it >= 2 && relmax <= 1e-4 && relmax >= 0.25 * prev_rel));
-      prev_rel = relmax;
-    }
     if (conv) return it;
   }
   return -1;
 }
 
+// Source terms at the substep start from the stored equilibrium (x_e, x_C+, x_CO),
+// with the dust temperature solved; gives the substep length of Sec. 6.1.
 template <class F>
-TCG_FN void substep_newton(const CellC<double>& c, const CellC<F>& cf, const DevParams& p, double dt,
-                                               LaneState& s, F& xe_g, F& td_g) {
-  // substep length from the source terms at the current state (stored equilibrium)
+TCG_FN void start_sources(const CellC<F>& cf, const DevParams& p, const LaneState& s, F& td_g, double& H0,
+                          double& CH2, double& CHp) {
   const double T = s.mu * s.Tmu;
-  const double e = c.K * s.Tmu;
-  double H0, CH2, CHp;
-  {
-    ChemT<F> b = chem_T(cf, F(T), p.flags);
-    CoolT<F> k = cool_T(cf, b, p.flags);
-    Equil<F> q;
-    q.xe = F(s.xe); q.xCp = F(s.xCp); q.xCO = F(s.xCO);
-    q.xOp = cf.xOtot * F(s.xHp);
-    q.xC = cf.xCtot - q.xCp - q.xCO;
-    q.xO = cf.xOtot - q.xCO - q.xOp;
-    Src<F> sr = source(cf, b, k, F(s.xH2), F(s.xHp), q, F(-1), td_g);
-    td_g = sr.Td;
-    H0 = double(sr.H); CH2 = double(sr.CH2); CHp = double(sr.CHp);
-  }
-  bool last;
-  double dts = substep_len(p, dt - s.t, e, H0, CH2, CHp, last);
+  ChemT<F> b = chem_T(cf, F(T), p.flags);
+  CoolT<F> k = cool_T(cf, b, p.flags);
+  Equil<F> q;
+  q.xe = F(s.xe); q.xCp = F(s.xCp); q.xCO = F(s.xCO);
+  q.xOp = cf.xOtot * F(s.xHp);
+  q.xC = cf.xCtot - q.xCp - q.xCO;
+  q.xO = cf.xOtot - q.xCO - q.xOp;
+  Src<F> sr = source(cf, b, k, F(s.xH2), F(s.xHp), F(1.0 - 2.0 * s.xH2 - s.xHp), q, F(-1), td_g);
+  td_g = sr.Td;
+  const double n = double(cf.n);
+  H0 = n * double(sr.G) - n * n * double(sr.L);
+  CH2 = double(sr.form) - double(sr.dest);
+  CHp = double(sr.ion) - double(sr.rec);
+}
+
+// Accepts the substep's root y: applies the temperature floor, re-solves the C/O/e
+// equilibrium at the new state in precision F and updates mu.
+template <class F>
+TCG_FN void finish_substep(const CellC<F>& cf, double muH, const DevParams& p, double dt, double dts, bool last,
+                           const double* y, LaneState& s) {
+  s.nsub += 1;
+  s.Tmu = fmax(y[0], p.T_floor / s.mu);
+  s.xH2 = y[1];
+  s.xHp = y[2];
+  ChemT<F> b1 = chem_T(cf, F(s.mu * s.Tmu), p.flags);
+  Equil<F> q = equilibrium(cf, b1, F(s.xH2), F(s.xHp), F(s.xe));
+  s.xe = double(q.xe); s.xCp = double(q.xCp); s.xCO = double(q.xCO);
+  s.mu = muH / (1.1 + s.xe - s.xH2);
+  s.t = last ? dt : s.t + dts;
+}
+
+// Solves one substep of length dts by the FP64 Newton iteration; a failed solve is
+// retried at half length (up to 30 times) and the cell flagged ST_NEWTON.
+TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double dt, double dts, bool last,
+                            LaneState& s, double& xe_g, double& td_g) {
   const double yn[3] = {s.Tmu, s.xH2, s.xHp};
   const double Kinv = 1.0 / c.K;
   double y[3] = {yn[0], yn[1], yn[2]};
-  int it = newton_solve<F>(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g);
+  int it = newton_solve(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g);
   int halv = 0;
   while (it < 0 && halv < 30) {
     s.status |= ST_NEWTON;
@@ -298,34 +327,185 @@ TCG_FN void substep_newton(const CellC<double>& c, const CellC<F>& cf, const Dev
     last = false;
     ++halv;
     y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2];
-    it = newton_solve<F>(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g);
+    it = newton_solve(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g);
   }
   if (it < 0) {
     s.status |= ST_NONFIN;
     s.t = dt;
     return;
   }
-  s.nsub += 1;
-  s.Tmu = fmax(y[0], p.T_floor / s.mu);
-  s.xH2 = y[1];
-  s.xHp = y[2];
-  // C/O/e equilibrium at the new state and new mu (FP64 in both precisions: it sets mu)
-  ChemT<double> b1 = chem_T(c, s.mu * s.Tmu, p.flags);
-  Equil<double> q = equilibrium(c, b1, s.xH2, s.xHp, s.xe);
-  s.xe = q.xe; s.xCp = q.xCp; s.xCO = q.xCO;
-  s.mu = c.muH / (1.1 + q.xe - s.xH2);
-  s.t = last ? dt : s.t + dts;
+  finish_substep<double>(c, c.muH, p, dt, dts, last, y, s);
+}
+
+TCG_FN void substep_newton64(const CellC<double>& c, const DevParams& p, double dt, LaneState& s, double& xe_g,
+                             double& td_g) {
+  double H0, CH2, CHp;
+  start_sources<double>(c, p, s, td_g, H0, CH2, CHp);
+  bool last;
+  const double dts = substep_len(p, dt - s.t, c.K * s.Tmu, H0, CH2, CHp, last);
+  solve_substep64(c, p, dt, dts, last, s, xe_g, td_g);
+}
+
+// ------------------------------------------------------------------ mode 2: mixed precision
+// f(y) from FP32 source terms; the closure x_H and the net sums H = n G - n^2 L,
+// C_H2 = form - dest, C_H+ = ion - rec are formed in FP64 from the FP32 parts.
+TCG_FN void feval32(const CellC<float>& cf, const ChemT<float>& b, const CoolT<float>& k, double y1, double y2,
+                    double Kinv, float& xe_guess, float& td_guess, double* f) {
+  const double xH = 1.0 - 2.0 * y1 - y2;
+  Equil<float> q = equilibrium(cf, b, float(y1), float(y2), xe_guess);
+  Src<float> s = source(cf, b, k, float(y1), float(y2), float(xH), q, -1.f, td_guess);
+  xe_guess = q.xe;
+  td_guess = s.Td;
+  const double n = double(cf.n);
+  f[0] = (n * double(s.G) - n * n * double(s.L)) * Kinv;
+  f[1] = double(s.form) - double(s.dest);
+  f[2] = double(s.ion) - double(s.rec);
+}
+
+// Mixed Newton on the same residual: FP32 source evaluations, FP64 residual, solve and
+// update.  The forward-difference Jacobian (relative step 1e-3, large enough that FP32
+// rounding in f stays ~1e-4 of each column) is built at the first iteration and reused;
+// it is rebuilt (at most twice) when the steps contract by less than a factor 0.3.
+// Returns the iteration count with polish = false when every step fell below
+// rtol_mixed |y_i| (+1e-12 for the abundances); with polish = true when the steps
+// stopped contracting above that, at the FP32 rounding floor of f (below 1e-4
+// relative), which happens near stiff equilibria where H or C_s is a small difference
+// of large terms; or -1 if neither happened.  J holds the last Jacobian on return.
+TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, double Kinv, const double* yn,
+                        double dts, double* y, float& xe_g, float& td_g, double J[3][3], bool& polish) {
+  bool haveJ = false;
+  int rebuilt = 0;
+  double prev = 1e300;
+  polish = false;
+  for (int it = 1; it <= p.newton_max; ++it) {
+    ChemT<float> b = chem_T(cf, float(mu * y[0]), p.flags);
+    CoolT<float> k = cool_T(cf, b, p.flags);
+    double f0[3];
+    feval32(cf, b, k, y[1], y[2], Kinv, xe_g, td_g, f0);
+    if (!haveJ) {
+#pragma unroll 1
+      for (int j = 1; j < 3; ++j) {
+        const double h = fmax(1e-3 * fabs(y[j]), 1e-12);
+        const double y1 = y[1] + ((j == 1) ? h : 0.0), y2 = y[2] + ((j == 2) ? h : 0.0);
+        float xg = xe_g, tg = td_g;
+        double fx[3];
+        feval32(cf, b, k, y1, y2, Kinv, xg, tg, fx);
+        for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - dts * (fx[i] - f0[i]) / h;
+      }
+      const double h = 1e-3 * y[0];
+      ChemT<float> bT = chem_T(cf, float(mu * (y[0] + h)), p.flags);
+      CoolT<float> kT = cool_T(cf, bT, p.flags);
+      float xg = xe_g, tg = td_g;
+      double fT[3];
+      feval32(cf, bT, kT, y[1], y[2], Kinv, xg, tg, fT);
+      for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - dts * (fT[i] - f0[i]) / h;
+      haveJ = true;
+    }
+    double Jw[3][3], rhs[3], d[3];
+    for (int i = 0; i < 3; ++i) {
+      rhs[i] = -(y[i] - yn[i] - dts * f0[i]);
+      for (int j = 0; j < 3; ++j) Jw[i][j] = J[i][j];
+    }
+    if (!solve3(Jw, rhs, d)) return -1;
+    double st[3];
+    const bool full = damped_step(y, d, st);
+    double nrm = 0.0;
+    for (int i = 0; i < 3; ++i)
+      nrm = fmax(nrm, fabs(st[i]) / (p.rtol_mixed * fabs(y[i]) + ((i == 0) ? 1e-300 : 1e-12)));
+    if (!finite3(y[0], y[1], y[2])) return -1;
+    if (full) {
+      if (nrm <= 1.0) return it;
+      if (it >= 2 && nrm > 0.3 * prev) {
+        if (nrm > 0.7 * prev && nrm * p.rtol_mixed <= 1e-4) {
+          polish = true;
+          return it;
+        }
+        if (rebuilt < 2) {
+          ++rebuilt;
+          haveJ = false;
+        }
+      }
+    }
+    prev = nrm;
+  }
+  return -1;
+}
+
+// FP64 polish of the mixed iteration's root: Newton corrections with the residual
+// evaluated entirely in FP64 and the last (FP32-built) Jacobian.  The FP32 root is
+// off the FP64 one by the FP32 rounding floor of f (~1e-6 relative in T near stiff
+// equilibria, where H is a small difference of large terms), and the scheme can
+// amplify such errors a hundredfold over a step, so every substep is polished.  The
+// chord iteration contracts by the Jacobian's relative error (<~0.1), so a correction
+// below 1e-7 relative leaves an error below ~1e-8: accept then, after at most three.
+// Returns false if that does not happen.
+TCG_FN bool polish64(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
+                     double dts, double* y, const double J[3][3], double& xe_g, double& td_g) {
+  for (int it = 0; it < 3; ++it) {
+    ChemT<double> b = chem_T(c, mu * y[0], p.flags);
+    CoolT<double> k = cool_T(c, b, p.flags);
+    double f0[3];
+    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0);
+    double Jw[3][3], rhs[3], d[3];
+    for (int i = 0; i < 3; ++i) {
+      rhs[i] = -(y[i] - yn[i] - dts * f0[i]);
+      for (int j = 0; j < 3; ++j) Jw[i][j] = J[i][j];
+    }
+    if (!solve3(Jw, rhs, d)) return false;
+    double st[3];
+    const bool full = damped_step(y, d, st);
+    double nrm = 0.0;
+    for (int i = 0; i < 3; ++i) nrm = fmax(nrm, fabs(st[i]) / (1e-7 * fabs(y[i]) + ((i == 0) ? 1e-300 : 1e-12)));
+    if (!finite3(y[0], y[1], y[2])) return false;
+    if (full && nrm <= 1.0) return true;
+  }
+  return false;
+}
+
+// One mixed-precision substep.  FP64 work: the source terms at the substep start that
+// set its length (Sec. 6.1; the length decides where the trajectory is sampled, and a
+// 1e-6 error in it shifts every later state in time), the polish of the root, and the
+// C/O/e equilibrium that sets mu at the end.  FP32 work: every Newton iteration before
+// the polish and the Jacobian.  td64 carries the FP64 dust-temperature warm start.
+TCG_FN void substep_mixed(const CellC<double>& c, const CellC<float>& cf, const DevParams& p, double dt,
+                          LaneState& s, float& xe_g, float& td_g, double& td64, const double* seed) {
+  double H0, CH2, CHp;
+  start_sources<double>(c, p, s, td64, H0, CH2, CHp);
+  bool last;
+  const double dts = substep_len(p, dt - s.t, c.K * s.Tmu, H0, CH2, CHp, last);
+  const double yn[3] = {s.Tmu, s.xH2, s.xHp};
+  const double Kinv = 1.0 / c.K;
+  double y[3] = {yn[0], yn[1], yn[2]};
+  if (seed) { y[0] = seed[0]; y[1] = seed[1]; y[2] = seed[2]; }
+  double J[3][3];
+  bool polish = false;
+  int it = newton_mixed(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, J, polish);
+  if (it >= 0) {
+    if (polish) s.status |= ST_POLISH;
+    double xg = double(xe_g), tg = double(td_g);
+    if (!polish64(c, p, s.mu, Kinv, yn, dts, y, J, xg, tg)) it = -1;
+  }
+  if (it < 0) {
+    // The plain FP64 solver finishes this substep (same length, same start state).
+    s.status |= ST_FALLBACK;
+    double xg = s.xe, tg = td64;
+    solve_substep64(c, p, dt, dts, last, s, xg, tg);
+  } else {
+    finish_substep<double>(c, c.muH, p, dt, dts, last, y, s);
+  }
+  xe_g = float(s.xe);
 }
 
 // ------------------------------------------------------------------ the kernel
 template <int MODE, bool BATCH>
 __global__ void __launch_bounds__(128) k_step(DevFields f1, const BoxTable* __restrict__ boxes, DevParams p,
                                                double dt, unsigned long long* cursor, long long ntotal) {
-  using F = typename std::conditional<MODE == 2, float, double>::type;
   LaneState s;
   CellC<double> c;
   CellC<float> cf;   // FP32 copy of the cell constants (mixed mode only)
-  F xe_g = F(-1), td_g = F(-1);
+  double xe_g = -1.0, td_g = -1.0;
+  float xe_gf = -1.f, td_gf = -1.f;
+  double td64 = -1.0;
   DevFields fb;
   long long li = -1;   // local cell index within its box
   bool have = false;
@@ -347,19 +527,27 @@ __global__ void __launch_bounds__(128) k_step(DevFields f1, const BoxTable* __re
       }
       double T0, x20, xp0;
       load_cell(fb, li, p, c, T0, x20, xp0);
-      if constexpr (MODE == 2) cf = cast_cell<float>(c);
-      ChemT<double> b0 = chem_T(c, T0, p.flags);
-      Equil<double> q0 = equilibrium(c, b0, x20, xp0, -1.0);
       s.t = 0.0;
       s.xH2 = x20; s.xHp = xp0;
-      s.xe = q0.xe; s.xCp = q0.xCp; s.xCO = q0.xCO;
-      s.mu = c.muH / (1.1 + q0.xe - x20);
-      s.Tmu = T0 / s.mu;
       s.Td = -1.0;
       s.nsub = 0;
       s.status = 0;
-      xe_g = F(q0.xe);
-      td_g = F(-1);
+      {
+        // initial C/O/e equilibrium (it sets mu and hence T_mu) in FP64 for every mode
+        ChemT<double> b0 = chem_T(c, T0, p.flags);
+        Equil<double> q0 = equilibrium(c, b0, x20, xp0, -1.0);
+        s.xe = q0.xe; s.xCp = q0.xCp; s.xCO = q0.xCO;
+        xe_g = q0.xe;
+        td_g = -1.0;
+      }
+      if constexpr (MODE == 2) {
+        cf = cast_cell<float>(c);
+        xe_gf = float(s.xe);
+        td_gf = -1.f;
+        td64 = -1.0;
+      }
+      s.mu = c.muH / (1.1 + s.xe - x20);
+      s.Tmu = T0 / s.mu;
       have = true;
     }
     if (s.t < dt) {
@@ -369,9 +557,9 @@ __global__ void __launch_bounds__(128) k_step(DevFields f1, const BoxTable* __re
       } else if constexpr (MODE == 0) {
         substep_paper(c, p, dt, s);
       } else if constexpr (MODE == 1) {
-        substep_newton<double>(c, c, p, dt, s, xe_g, td_g);
+        substep_newton64(c, p, dt, s, xe_g, td_g);
       } else {
-        substep_newton<float>(c, cf, p, dt, s, xe_g, td_g);
+        substep_mixed(c, cf, p, dt, s, xe_gf, td_gf, td64, nullptr);
       }
       if (!finite3(s.Tmu, s.xH2, s.xHp)) {
         s.status |= ST_NONFIN;

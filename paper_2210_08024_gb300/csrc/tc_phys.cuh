@@ -403,10 +403,12 @@ template <class F> struct HRate {
   F Rr;    // alpha_rr n_e + alpha_gr n
 };
 
-template <class F> TCG_FN HRate<F> h_rates(const CellC<F>& c, const ChemT<F>& b, F xH2, F xHp,
+// xH is the atomic fraction 1 - 2 x_H2 - x_H+ (Sec. 3.1.3), passed in so that the
+// mixed-precision path can form it in FP64 and hand the FP32 rates an accurate value
+// when x_H+ -> 1 or x_H2 -> 1/2.
+template <class F> TCG_FN HRate<F> h_rates(const CellC<F>& c, const ChemT<F>& b, F xH2, F xH,
                                                                F xe, F lpsi) {
   HRate<F> r;
-  F xH = F(1) - F(2) * xH2 - xHp;
   F zcrH2 = F(2) * c.xi * (F(2.3) * xH2 + F(1.5) * xH);        // Eq. eq:H2_cr
   F zcd = c.n * (b.kcdH * xH + b.kcdH2 * xH2);
   F ne = xe * c.n;
@@ -428,21 +430,28 @@ template <class F> struct Src {
   F H;          // n Gamma - n^2 Lambda [erg cm^-3 s^-1]
   F CH2, CHp;   // Eqs. e:HH, e:HII [s^-1]
   F Td;
+  F G, L;       // heating per H [erg s^-1] and cooling per n_H^2 [erg cm^3 s^-1]
+  F form, dest; // k_gr n x_H and D_H2 x_H2: the two sides of Eq. e:HH
+  F ion, rec;   // I x_H and R x_H+: the two sides of Eq. e:HII
 };
 
-// Heating (Eq. e:heating) and cooling (Eq. eq:cooling_fnct) at (T, x_H2, x_H+, q).
-// Td_fixed > 0 freezes the dust temperature; otherwise it is solved from Td_guess.
+// Heating (Eq. e:heating) and cooling (Eq. eq:cooling_fnct) at (T, x_H2, x_H+, q) with
+// the atomic fraction xH given.  Td_fixed > 0 freezes the dust temperature; otherwise it
+// is solved from Td_guess.
 template <class F> TCG_FN Src<F> source(const CellC<F>& c, const ChemT<F>& b, const CoolT<F>& k,
-                                                            F xH2, F xHp, const Equil<F>& q, F Td_fixed,
+                                                            F xH2, F xHp, F xH, const Equil<F>& q, F Td_fixed,
                                                             F Td_guess) {
   Src<F> s;
   const F n = c.n;
   const F xe = q.xe;
-  const F xH = F(1) - F(2) * xH2 - xHp;
   const F lp = log_psi(c, b, xe);
-  const HRate<F> r = h_rates(c, b, xH2, xHp, xe, lp);
-  s.CH2 = r.kn * xH - r.DH2 * xH2;
-  s.CHp = r.I * xH - r.Rr * xHp;
+  const HRate<F> r = h_rates(c, b, xH2, xH, xe, lp);
+  s.form = r.kn * xH;
+  s.dest = r.DH2 * xH2;
+  s.ion = r.I * xH;
+  s.rec = r.Rr * xHp;
+  s.CH2 = s.form - s.dest;
+  s.CHp = s.ion - s.rec;
   // --- heating per H
   F eps = k.eps_num / (F(1) + F(0.04996) * m_exp(F(0.431) * lp) * (F(1) + F(0.00430) * m_exp(F(0.692) * lp)));
   F qH = (F(7.5) + F(24.5) * m_sqrt(xe / (xe + F(0.07)))) * F(EV);
@@ -460,7 +469,12 @@ template <class F> TCG_FN Src<F> source(const CellC<F>& c, const ChemT<F>& b, co
   {
     F nL = n * k.rvLlow;                                                // H2 ro-vibrational
     F den = nL + k.rvLLTE;
-    Lhyd += (den > F(0)) ? xH2 * (k.rvLLTE * nL / den) / n : F(0);
+    // harmonic combination L_LTE n L_low / (n L_low + L_LTE); in FP32 the product of the
+    // two rates (~1e-22 x 1e-24) underflows, so the ratio is taken first there.
+    F Lrv;
+    if constexpr (sizeof(F) == 4) Lrv = k.rvLLTE * (nL / den);
+    else Lrv = k.rvLLTE * nL / den;
+    Lhyd += (den > F(0)) ? xH2 * Lrv / n : F(0);
   }
   F Lmet;
   {
@@ -507,6 +521,8 @@ template <class F> TCG_FN Src<F> source(const CellC<F>& c, const ChemT<F>& b, co
     Lmet += F(3.2e-34) * b.sqT * (b.T - s.Td) * c.Zd;
   }
   F L = Lhyd + (F(1) - b.S) * Lmet + b.S * k.cie;
+  s.G = G;
+  s.L = L;
   s.H = n * G - n * n * L;
   return s;
 }

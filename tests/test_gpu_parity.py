@@ -94,7 +94,7 @@ def test_host_buffer_entry_matches_device(tc, cfg1):
     st.close()
 
 
-def test_batched_boxes_match_single_launches(tc):
+def test_batched_boxes_match_oracle_and_replay(tc):
     import torch
     boxes = [synthgen.cells_4096(n=n, key=300 + i, Z=z) for i, (n, z) in enumerate([(512, 0.3), (1000, 1.0), (77, 2.5)])]
     st = tc.Stepper(tc.TC_MODE_PAPER_FP64)
@@ -105,10 +105,12 @@ def test_batched_boxes_match_single_launches(tc):
     fields = [tc.make_fields(d, Zg=float(b["Zg"][0]), Zd=float(b["Zd"][0])) for d, b in zip(devs, boxes)]
     tc.tc_step_batch(st.h, fields, DT)
     torch.cuda.synchronize()
+    # Each box against the oracle at its own metallicity.  (The batched kernel is a
+    # separate instantiation; FMA contraction may differ from the single-box kernel at
+    # the rounding level, so the bar is the parity tolerance, not bit equality.)
     for d, b in zip(devs, boxes):
-        g = tc.step_numpy(b, DT, tc.TC_MODE_PAPER_FP64)
-        for k in ("T", "xH2", "xHp"):
-            assert np.array_equal(d[k].cpu().numpy(), g[k]), k
+        ref, spread = ulp_spread(oracle, b, DT, oracle.default_params(mode=0))
+        assert_fp64_parity({k: d[k].cpu().numpy() for k in ("T", "xH2", "xHp")}, ref, "batch", spread=spread)
     # replay of the captured graph on restored inputs gives the same answer
     first = [d["T"].clone() for d in devs]
     for d, b in zip(devs, boxes):
