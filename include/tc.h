@@ -123,6 +123,28 @@ int tc_step_batch(tc_handle *h, const tc_fields *boxes, int nbox, double dt_s, v
  * synchronises `stream` before returning. */
 int tc_step_host(tc_handle *h, const tc_fields *f, double dt_s, void *stream);
 
+/* Largest ncell that tc_step_host_static accepts. */
+#define TC_STATIC_MAX_CELLS 65536
+
+/* tc_step_host_static -- the paper has no counterpart: this is a service of the library.
+ * It is tc_step_host for callers that may not allocate device memory: for instance a code
+ * running inside another application's fixed device-memory budget, or one whose device
+ * allocator belongs to someone else.  It needs no handle and calls no cudaMalloc or
+ * cudaFree.  Its device staging (inputs, state, outputs) and the work-queue cursor of the
+ * step kernel live in one file-scope device array sized for TC_STATIC_MAX_CELLS cells
+ * (~8.4 MB).  Every GPU that loads the library holds that array until the process exits.
+ *  - p: parameters as for tc_create (modes TC_MODE_PAPER_FP64, TC_MODE_NEWTON_FP64 and
+ *    TC_MODE_MIXED; seeded modes are rejected).  f: HOST pointers as for tc_step_host.
+ *  - Copies the inputs in, runs one step of dt_s seconds on `stream`, copies T, x_h2,
+ *    x_hp and the optional outputs back, and synchronises `stream` before returning.
+ *  - Returns TC_EINVAL if ncell > TC_STATIC_MAX_CELLS, for NULL required pointers, a bad
+ *    mode or a negative or non-finite dt_s; TC_ECUDA if a CUDA call fails.
+ *  - The first call on a device looks up the array's device address (once per device,
+ *    with that device current).  Make that first call before any stream capture.
+ *  - All calls share the array, and each call overwrites what the last one left.  Calls
+ *    that overlap on the GPU (other streams or host threads) race: serialise them. */
+int tc_step_host_static(const tc_params *p, const tc_fields *f, double dt_s, void *stream);
+
 /* Loads MLP seed weights (the blob written by tc_mlp_export) into the handle. */
 int tc_load_mlp(tc_handle *h, const void *blob, size_t bytes);
 

@@ -85,6 +85,8 @@ def _load():
     L.tc_peak_launch.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                  ctypes.c_void_p]
     L.tc_peak_chains.restype = ctypes.c_int
+    L.tc_step_host_static.argtypes = [ctypes.POINTER(tc_params), ctypes.POINTER(tc_fields), ctypes.c_double,
+                                      ctypes.c_void_p]
     return L
 
 
@@ -180,6 +182,21 @@ def tc_step(h, fields: tc_fields, dt: float, stream=None) -> None:
 
 def tc_step_host(h, fields: tc_fields, dt: float, stream=None) -> None:
     _check(lib.tc_step_host(h, ctypes.byref(fields), float(dt), _stream_ptr(stream)), "tc_step_host")
+
+
+TC_STATIC_MAX_CELLS = 65536
+
+
+def tc_step_host_static(params: tc_params, fields: tc_fields, dt: float, stream=None) -> None:
+    """tc_step_host without a handle and without any device allocation: for callers
+    that hold host arrays but may not allocate device memory.  The library's static
+    device scratch holds at most TC_STATIC_MAX_CELLS cells; calls share it, so calls
+    that overlap on the GPU race."""
+    if fields.ncell > TC_STATIC_MAX_CELLS:
+        raise ValueError("tc_step_host_static: ncell %d exceeds the static scratch capacity of %d cells"
+                         % (fields.ncell, TC_STATIC_MAX_CELLS))
+    _check(lib.tc_step_host_static(ctypes.byref(params), ctypes.byref(fields), float(dt), _stream_ptr(stream)),
+           "tc_step_host_static")
 
 
 def tc_step_batch(h, boxes: list, dt: float, stream=None) -> None:
