@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--side", type=int, default=128)
-    ap.add_argument("--modes", default="newton,mixed,paper", help="comma list of modes to time (first = headline)")
+    ap.add_argument("--modes", default="newton,mixed,mixed_seeded,newton_seeded,paper",
+                    help="comma list of modes to time (first = headline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-peaks", action="store_true", help="skip the pipe microbenchmarks (no roofline)")
@@ -176,8 +177,11 @@ def run_gpu(args):
     dev = tc.to_device(cells)
     pristine = {k: dev[k].clone() for k in STATE_KEYS}
     stream = torch.cuda.current_stream()
-    mode_ids = {"newton": tc.TC_MODE_NEWTON_FP64, "paper": tc.TC_MODE_PAPER_FP64, "mixed": tc.TC_MODE_MIXED}
-    modes = [m for m in args.modes.split(",") if m]
+    mode_ids = {"newton": tc.TC_MODE_NEWTON_FP64, "paper": tc.TC_MODE_PAPER_FP64, "mixed": tc.TC_MODE_MIXED,
+                "newton_seeded": tc.TC_MODE_NEWTON_FP64_SEEDED, "mixed_seeded": tc.TC_MODE_MIXED_SEEDED}
+    from paper_2210_08024_gb300 import seed_net
+    blob = open(seed_net.DEFAULT_BLOB, "rb").read() if os.path.exists(seed_net.DEFAULT_BLOB) else None
+    modes = [m for m in args.modes.split(",") if m and (blob is not None or "seeded" not in m)]
     peaks = measure_peaks(tc, torch) if (rank == 0 and not args.no_peaks) else None
 
     def restore():
@@ -188,6 +192,8 @@ def run_gpu(args):
     clocks = None
     for mi, mname in enumerate(modes):
         st = tc.Stepper(mode_ids[mname])
+        if "seeded" in mname:
+            st.load_mlp(blob)
         f = tc.make_fields(dev)
         for _ in range(args.warmup):
             restore()
@@ -225,7 +231,8 @@ def run_gpu(args):
         nbad = tc.tc_sync_status(st.h, dev["status"])
         results[mname] = {"ms_per_step": ms / args.steps, "kernel_ms": float(np.mean(kms)),
                           "value": ws * ncell * args.steps / (ms * 1e-3), "launches": launches,
-                          "cells_not_ok": nbad, "mode_id": mode_ids[mname]}
+                          "cells_not_ok": nbad, "newton_iters_per_cell": float(dev["iters"].double().mean().item()),
+                          "mode_id": mode_ids[mname]}
         st.close()
 
     head = modes[0]

@@ -96,6 +96,8 @@ typedef struct tc_fields {
   int *nsub, *status;
   long long ncell;
   double Zg_val, Zd_val;    /* scalars used when Zg / Zd are NULL */
+  int *newton_iters;        /* optional out (device, may be NULL): Newton iterations summed over the
+                               cell's substeps (modes 1-4; the mixed modes count FP32 iterations) */
 } tc_fields;
 
 typedef struct tc_handle tc_handle;
@@ -145,7 +147,9 @@ int tc_step_host(tc_handle *h, const tc_fields *f, double dt_s, void *stream);
  *    that overlap on the GPU (other streams or host threads) race: serialise them. */
 int tc_step_host_static(const tc_params *p, const tc_fields *f, double dt_s, void *stream);
 
-/* Loads MLP seed weights (the blob written by tc_mlp_export) into the handle. */
+/* Loads the seed network's weights (the blob written by tc_mlp_export, include/tc_mlp.h,
+ * exactly tc_mlp_blob_bytes() bytes) into the handle; TC_EINVAL for a blob of another
+ * size or layout version.  Required before a step in a seeded mode. */
 int tc_load_mlp(tc_handle *h, const void *blob, size_t bytes);
 
 /* Counts cells whose status has any TC_ST_ERROR_MASK bit in the last step's status array

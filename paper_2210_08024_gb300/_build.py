@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtc_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["tc_api.cu", "tc_k_paper.cu", "tc_k_newton.cu", "tc_k_mixed.cu", "tc_mlp.cu", "tc_peak.cu",
-           "tc_static.cu"]
+           "tc_static.cu", "tc_k_seeded.cu"]
 
 
 def nvcc() -> str:
@@ -44,7 +44,8 @@ def _stale() -> bool:
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    deps.append(os.path.join(os.path.dirname(HERE), "include", "tc.h"))
+    inc = os.path.join(os.path.dirname(HERE), "include")
+    deps += [os.path.join(inc, f) for f in os.listdir(inc)]
     deps.append(__file__)
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 

@@ -18,6 +18,8 @@ namespace tcg {
 int occupancy_mode0_impl(int block);
 int occupancy_mode1_impl(int block);
 int occupancy_mode2_impl(int block);
+int occupancy_mode3_impl(int block);
+int occupancy_mode4_impl(int block);
 }  // namespace tcg
 
 struct tc_handle {
@@ -155,13 +157,21 @@ static tcg::DevFields dev_fields(const tc_fields* f) {
   d.n = f->n; d.chi_pe = f->chi_pe; d.chi_lw = f->chi_lw; d.fh2 = f->f_shld_h2; d.fc = f->f_shld_c;
   d.Flyc = f->F_lyc; d.xi = f->xi_cr; d.Zg = f->Zg; d.Zd = f->Zd;
   d.T = f->T; d.xH2 = f->x_h2; d.xHp = f->x_hp; d.xe = f->x_e; d.xCp = f->x_cp; d.xCO = f->x_co;
-  d.nsub = f->nsub; d.status = f->status;
+  d.nsub = f->nsub; d.status = f->status; d.iters = f->newton_iters;
   d.ncell = f->ncell;
   d.Zg_val = f->Zg_val; d.Zd_val = f->Zd_val;
   return d;
 }
 
-static int kernel_mode(int mode) { return (mode == TC_MODE_PAPER_FP64) ? 0 : (mode == TC_MODE_MIXED || mode == TC_MODE_MIXED_SEEDED) ? 2 : 1; }
+static int kernel_mode(int mode) {
+  switch (mode) {
+    case TC_MODE_PAPER_FP64: return 0;
+    case TC_MODE_NEWTON_FP64: return 1;
+    case TC_MODE_MIXED: return 2;
+    case TC_MODE_MIXED_SEEDED: return 3;
+    default: return 4;  // TC_MODE_NEWTON_FP64_SEEDED
+  }
+}
 
 static void launch_shape(tc_handle* h, int kmode, long long ntotal, int* grid, int* block) {
   int b = h->p.block > 0 ? h->p.block : 128;
@@ -170,8 +180,10 @@ static void launch_shape(tc_handle* h, int kmode, long long ntotal, int* grid, i
   if (b < 32) b = 32;
   int per_sm = h->p.blocks_per_sm;
   if (per_sm <= 0) {
-    per_sm = (kmode == 0) ? tcg::occupancy_mode0_impl(b) : (kmode == 1) ? tcg::occupancy_mode1_impl(b)
-                                                                        : tcg::occupancy_mode2_impl(b);
+    per_sm = (kmode == 0) ? tcg::occupancy_mode0_impl(b)
+             : (kmode == 1) ? tcg::occupancy_mode1_impl(b)
+             : (kmode == 2) ? tcg::occupancy_mode2_impl(b)
+             : (kmode == 3) ? tcg::occupancy_mode3_impl(b) : tcg::occupancy_mode4_impl(b);
   }
   long long g = (long long)h->num_sms * per_sm;
   long long need = (ntotal + b - 1) / b;
@@ -193,7 +205,13 @@ static int enqueue(tc_handle* h, bool batch, const tcg::DevFields& f, long long 
   cudaError_t e;
   if (kmode == 0) e = tcg::launch_mode0(batch, f, h->d_boxes, dp, dt, h->d_cursor, ntotal, grid, block, st);
   else if (kmode == 1) e = tcg::launch_mode1(batch, f, h->d_boxes, dp, dt, h->d_cursor, ntotal, grid, block, st);
-  else e = tcg::launch_mode2(batch, f, h->d_boxes, dp, dt, h->d_cursor, ntotal, grid, block, st);
+  else if (kmode == 2) e = tcg::launch_mode2(batch, f, h->d_boxes, dp, dt, h->d_cursor, ntotal, grid, block, st);
+  else if (kmode == 3)
+    e = tcg::launch_mode3(batch, f, h->d_boxes, dp, dt, h->d_cursor, ntotal, grid, block, st,
+                          (const tcg::MlpDev*)h->d_mlp);
+  else
+    e = tcg::launch_mode4(batch, f, h->d_boxes, dp, dt, h->d_cursor, ntotal, grid, block, st,
+                          (const tcg::MlpDev*)h->d_mlp);
   if (e != cudaSuccess) return TC_ECUDA;
   h->launches += 1;
   return TC_OK;
@@ -224,7 +242,7 @@ int tc_step_host(tc_handle* h, const tc_fields* f, double dt_s, void* stream) {
     h->d_ibuf = nullptr;
     h->d_buf_cells = 0;
     if (cudaMalloc(&h->d_buf, n * sizeof(double) * (NIN + NST)) != cudaSuccess) return TC_ENOMEM;
-    if (cudaMalloc(&h->d_ibuf, n * sizeof(int) * 2) != cudaSuccess) return TC_ENOMEM;
+    if (cudaMalloc(&h->d_ibuf, n * sizeof(int) * 3) != cudaSuccess) return TC_ENOMEM;
     h->d_buf_cells = n;
   }
   double* b = h->d_buf;
@@ -248,6 +266,7 @@ int tc_step_host(tc_handle* h, const tc_fields* f, double dt_s, void* stream) {
   d.T = dst[0]; d.x_h2 = dst[1]; d.x_hp = dst[2]; d.x_e = dst[3]; d.x_cp = dst[4]; d.x_co = dst[5];
   d.nsub = f->nsub ? h->d_ibuf : nullptr;
   d.status = f->status ? h->d_ibuf + n : nullptr;
+  d.newton_iters = f->newton_iters ? h->d_ibuf + 2 * n : nullptr;
   rc = enqueue(h, false, dev_fields(&d), f->ncell, dt_s, st);
   if (rc != TC_OK) return rc;
   for (int k = 0; k < NST; ++k)
@@ -256,6 +275,9 @@ int tc_step_host(tc_handle* h, const tc_fields* f, double dt_s, void* stream) {
   if (f->nsub && cudaMemcpyAsync(f->nsub, d.nsub, n * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return TC_ECUDA;
   if (f->status && cudaMemcpyAsync(f->status, d.status, n * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return TC_ECUDA;
+  if (f->newton_iters &&
+      cudaMemcpyAsync(f->newton_iters, d.newton_iters, n * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return TC_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return TC_ECUDA;
   return TC_OK;
@@ -330,7 +352,11 @@ int tc_step_batch(tc_handle* h, const tc_fields* boxes, int nbox, double dt_s, v
 }
 
 int tc_load_mlp(tc_handle* h, const void* blob, size_t bytes) {
-  if (!h || !blob || bytes == 0) return TC_EINVAL;
+  if (!h || !blob || bytes != sizeof(tcg::MlpDev)) return TC_EINVAL;
+  const tcg::MlpDev* hb = (const tcg::MlpDev*)blob;
+  if (hb->magic != tcg::MLP_MAGIC || hb->version != tcg::MLP_VERSION || hb->bytes != sizeof(tcg::MlpDev) ||
+      hb->n_in != (uint32_t)tcg::MLP_IN || hb->n_hid != (uint32_t)tcg::MLP_HID || hb->n_out != (uint32_t)tcg::MLP_OUT)
+    return TC_EINVAL;
   cudaFree(h->d_mlp);
   h->d_mlp = nullptr;
   if (cudaMalloc(&h->d_mlp, bytes) != cudaSuccess) return TC_ENOMEM;

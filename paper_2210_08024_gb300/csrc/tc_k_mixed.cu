@@ -6,9 +6,9 @@ namespace tcg {
 cudaError_t launch_mode2(bool batch, const DevFields& f, const BoxTable* d_boxes, const DevParams& p, double dt,
                          unsigned long long* cursor, long long ntotal, int grid, int block, cudaStream_t st) {
   if (batch)
-    k_step<2, true><<<grid, block, 0, st>>>(f, d_boxes, p, dt, cursor, ntotal);
+    k_step<2, true><<<grid, block, 0, st>>>(f, d_boxes, p, dt, cursor, ntotal, nullptr);
   else
-    k_step<2, false><<<grid, block, 0, st>>>(f, d_boxes, p, dt, cursor, ntotal);
+    k_step<2, false><<<grid, block, 0, st>>>(f, d_boxes, p, dt, cursor, ntotal, nullptr);
   return cudaGetLastError();
 }
 

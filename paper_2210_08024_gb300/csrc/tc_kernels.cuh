@@ -9,6 +9,8 @@
 //
 // MODE 0: the paper's sequential update (Sec. 6.1), FP64.
 // MODE 1: coupled backward Euler on (T_mu, x_H2, x_H+) by Newton, FP64.
+// MODE 3: as 2, each Newton solve started from the seed network's prediction.
+// MODE 4: as 1, each Newton solve started from the seed network's prediction.
 // MODE 2: as 1 with the rates, the C/O/e equilibrium and the heating/cooling sums in
 //         FP32, and the Newton update, its residual and the closure
 //         x_H = 1 - 2 x_H2 - x_H+ in FP64; a substep whose mixed solve does not
@@ -16,6 +18,7 @@
 #pragma once
 #include <type_traits>
 
+#include "tc_mlp.cuh"
 #include "tc_phys.cuh"
 
 namespace tcg {
@@ -23,7 +26,7 @@ namespace tcg {
 struct DevFields {
   const double *n, *chi_pe, *chi_lw, *fh2, *fc, *Flyc, *xi, *Zg, *Zd;
   double *T, *xH2, *xHp, *xe, *xCp, *xCO;
-  int *nsub, *status;
+  int *nsub, *status, *iters;
   long long ncell;
   double Zg_val, Zd_val;
 };
@@ -52,7 +55,7 @@ __device__ __forceinline__ long long claim_cells(unsigned long long* cursor) {
 struct LaneState {
   double t, Tmu, xH2, xHp, mu;
   double xe, xCp, xCO, Td;
-  int nsub, status;
+  int nsub, status, iters;
 };
 
 TCG_FN void load_cell(const DevFields& f, long long i, const DevParams& p, CellC<double>& c,
@@ -76,6 +79,7 @@ TCG_FN void store_cell(const DevFields& f, long long i, const LaneState& s) {
   if (f.xCO) f.xCO[i] = s.xCO;
   if (f.nsub) f.nsub[i] = s.nsub;
   if (f.status) f.status[i] = s.status;
+  if (f.iters) f.iters[i] = s.iters;
 }
 
 TCG_FN bool finite3(double a, double b, double c) {
@@ -312,14 +316,22 @@ TCG_FN void finish_substep(const CellC<F>& cf, double muH, const DevParams& p, d
   s.t = last ? dt : s.t + dts;
 }
 
-// Solves one substep of length dts by the FP64 Newton iteration; a failed solve is
-// retried at half length (up to 30 times) and the cell flagged ST_NEWTON.
+// Solves one substep of length dts by the FP64 Newton iteration, from `seed` when
+// given (the root is the same; a seeded solve that fails is retried from the start
+// state), else from the start state; a failed solve is retried at half length (up to
+// 30 times) and the cell flagged ST_NEWTON.
 TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double dt, double dts, bool last,
-                            LaneState& s, double& xe_g, double& td_g) {
+                            LaneState& s, double& xe_g, double& td_g, const double* seed = nullptr) {
   const double yn[3] = {s.Tmu, s.xH2, s.xHp};
   const double Kinv = 1.0 / c.K;
   double y[3] = {yn[0], yn[1], yn[2]};
-  int it = newton_solve(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g);
+  int it = -1;
+  if (seed) {
+    y[0] = seed[0]; y[1] = seed[1]; y[2] = seed[2];
+    it = newton_solve(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g);
+    if (it < 0) { y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2]; }
+  }
+  if (it < 0) it = newton_solve(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g);
   int halv = 0;
   while (it < 0 && halv < 30) {
     s.status |= ST_NEWTON;
@@ -334,15 +346,22 @@ TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double d
     s.t = dt;
     return;
   }
+  s.iters += it;
   finish_substep<double>(c, c.muH, p, dt, dts, last, y, s);
+}
+
+// Substep length of Sec. 6.1 from the FP64 source terms at the substep start.
+TCG_FN double substep_start64(const CellC<double>& c, const DevParams& p, double dt, const LaneState& s,
+                              double& td_g, bool& last) {
+  double H0, CH2, CHp;
+  start_sources<double>(c, p, s, td_g, H0, CH2, CHp);
+  return substep_len(p, dt - s.t, c.K * s.Tmu, H0, CH2, CHp, last);
 }
 
 TCG_FN void substep_newton64(const CellC<double>& c, const DevParams& p, double dt, LaneState& s, double& xe_g,
                              double& td_g) {
-  double H0, CH2, CHp;
-  start_sources<double>(c, p, s, td_g, H0, CH2, CHp);
   bool last;
-  const double dts = substep_len(p, dt - s.t, c.K * s.Tmu, H0, CH2, CHp, last);
+  const double dts = substep_start64(c, p, dt, s, td_g, last);
   solve_substep64(c, p, dt, dts, last, s, xe_g, td_g);
 }
 
@@ -466,13 +485,11 @@ TCG_FN bool polish64(const CellC<double>& c, const DevParams& p, double mu, doub
 // set its length (Sec. 6.1; the length decides where the trajectory is sampled, and a
 // 1e-6 error in it shifts every later state in time), the polish of the root, and the
 // C/O/e equilibrium that sets mu at the end.  FP32 work: every Newton iteration before
-// the polish and the Jacobian.  td64 carries the FP64 dust-temperature warm start.
-TCG_FN void substep_mixed(const CellC<double>& c, const CellC<float>& cf, const DevParams& p, double dt,
-                          LaneState& s, float& xe_g, float& td_g, double& td64, const double* seed) {
-  double H0, CH2, CHp;
-  start_sources<double>(c, p, s, td64, H0, CH2, CHp);
-  bool last;
-  const double dts = substep_len(p, dt - s.t, c.K * s.Tmu, H0, CH2, CHp, last);
+// the polish and the Jacobian.  The solve starts from `seed` when given, else from the
+// start state.
+TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<float>& cf, const DevParams& p, double dt,
+                                double dts, bool last, LaneState& s, float& xe_g, float& td_g, double td64,
+                                const double* seed) {
   const double yn[3] = {s.Tmu, s.xH2, s.xHp};
   const double Kinv = 1.0 / c.K;
   double y[3] = {yn[0], yn[1], yn[2]};
@@ -491,18 +508,76 @@ TCG_FN void substep_mixed(const CellC<double>& c, const CellC<float>& cf, const 
     double xg = s.xe, tg = td64;
     solve_substep64(c, p, dt, dts, last, s, xg, tg);
   } else {
+    s.iters += it;
     finish_substep<double>(c, c.muH, p, dt, dts, last, y, s);
   }
   xe_g = float(s.xe);
 }
 
+TCG_FN void substep_mixed(const CellC<double>& c, const CellC<float>& cf, const DevParams& p, double dt,
+                          LaneState& s, float& xe_g, float& td_g, double& td64) {
+  bool last;
+  const double dts = substep_start64(c, p, dt, s, td64, last);
+  substep_mixed_solve(c, cf, p, dt, dts, last, s, xe_g, td_g, td64, nullptr);
+}
+
+// ------------------------------------------------------------------ seeding (modes 3, 4)
+#ifdef __CUDACC__
+// Shared-memory footprint of the seeded kernels for `block` threads: the weights and
+// two [64][block] activation buffers.
+__host__ __device__ constexpr size_t seed_smem_bytes(int block) {
+  return sizeof(MlpDev) + 2 * (size_t)MLP_HID * block * sizeof(float);
+}
+
+// Seed of a substep's Newton iteration from the network: features of the substep start
+// (state, per-cell field features lf[5] = log10 n, log10 chi_FUV, log10 f_shld,H2,
+// log10(F_LyC+1), log10 xi) and its length; outputs mapped to (T_mu, x_H2, x_H+) with
+// mu frozen at the substep start and clamped inside the admissible region.  Returns
+// false (no seed) if the prediction is not finite.
+__device__ __forceinline__ bool mlp_seed(const MlpDev* w, float* buf0, float* buf1, int st, const float* lf,
+                                         const LaneState& s, double dts, const DevParams& p, double* seed) {
+  const double T0 = s.mu * s.Tmu;
+  float f[MLP_IN] = {lf[0], (float)log10(T0), (float)s.xH2, (float)s.xHp, lf[1], lf[2], lf[3], lf[4],
+                     (float)log10(dts)};
+  float o[MLP_OUT];
+  mlp_infer(w, buf0, buf1, st, f, o);
+  if (!(isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]))) return false;
+  const double x2 = fmin(fmax(0.5 * (double)o[0], 1e-20), 0.4999999);
+  const double xp = fmin(fmax((double)o[1], 1e-20), 0.999999 * (1.0 - 2.0 * x2));
+  const double T1 = fmin(fmax(T0 * exp10((double)fmin(fmax(o[2], -6.f), 6.f)), p.T_floor), 1e10);
+  seed[0] = T1 / s.mu;
+  seed[1] = x2;
+  seed[2] = xp;
+  return true;
+}
+#endif
+
 // ------------------------------------------------------------------ the kernel
 template <int MODE, bool BATCH>
 __global__ void __launch_bounds__(128) k_step(DevFields f1, const BoxTable* __restrict__ boxes, DevParams p,
-                                               double dt, unsigned long long* cursor, long long ntotal) {
+                                               double dt, unsigned long long* cursor, long long ntotal,
+                                               const MlpDev* __restrict__ mlp) {
+  constexpr bool SEEDED = (MODE == 3 || MODE == 4);
+  constexpr bool MIXED = (MODE == 2 || MODE == 3);
+  extern __shared__ __align__(16) unsigned char smem[];
+  const MlpDev* wsm = nullptr;
+  float* buf0 = nullptr;
+  float* buf1 = nullptr;
+  if constexpr (SEEDED) {
+    // weights to shared memory once per block
+    const int4* src = reinterpret_cast<const int4*>(mlp);
+    int4* dst = reinterpret_cast<int4*>(smem);
+    for (int i = threadIdx.x; i < (int)(sizeof(MlpDev) / 16); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    wsm = reinterpret_cast<const MlpDev*>(smem);
+    float* act = reinterpret_cast<float*>(smem + sizeof(MlpDev));
+    buf0 = act + threadIdx.x;
+    buf1 = act + (size_t)MLP_HID * blockDim.x + threadIdx.x;
+  }
+  float lf[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   LaneState s;
   CellC<double> c;
-  CellC<float> cf;   // FP32 copy of the cell constants (mixed mode only)
+  CellC<float> cf;   // FP32 copy of the cell constants (mixed modes)
   double xe_g = -1.0, td_g = -1.0;
   float xe_gf = -1.f, td_gf = -1.f;
   double td64 = -1.0;
@@ -532,6 +607,7 @@ __global__ void __launch_bounds__(128) k_step(DevFields f1, const BoxTable* __re
       s.Td = -1.0;
       s.nsub = 0;
       s.status = 0;
+      s.iters = 0;
       {
         // initial C/O/e equilibrium (it sets mu and hence T_mu) in FP64 for every mode
         ChemT<double> b0 = chem_T(c, T0, p.flags);
@@ -540,11 +616,20 @@ __global__ void __launch_bounds__(128) k_step(DevFields f1, const BoxTable* __re
         xe_g = q0.xe;
         td_g = -1.0;
       }
-      if constexpr (MODE == 2) {
+      if constexpr (MIXED) {
         cf = cast_cell<float>(c);
         xe_gf = float(s.xe);
         td_gf = -1.f;
         td64 = -1.0;
+      }
+      if constexpr (SEEDED) {
+        const double chi_fuv = (1.8e-4 * fb.chi_pe[li] + 3.0e-5 * fb.chi_lw[li]) / 2.1e-4;
+        const double Fl = fb.Flyc ? fb.Flyc[li] : 0.0;
+        lf[0] = (float)log10(fb.n[li]);
+        lf[1] = (float)log10(fmax(chi_fuv, 1e-30));
+        lf[2] = (float)log10(fmax(fb.fh2[li], 1e-30));
+        lf[3] = (float)log10(Fl + 1.0);
+        lf[4] = (float)log10(fmax(fb.xi[li], 1e-30));
       }
       s.mu = c.muH / (1.1 + s.xe - x20);
       s.Tmu = T0 / s.mu;
@@ -558,8 +643,17 @@ __global__ void __launch_bounds__(128) k_step(DevFields f1, const BoxTable* __re
         substep_paper(c, p, dt, s);
       } else if constexpr (MODE == 1) {
         substep_newton64(c, p, dt, s, xe_g, td_g);
+      } else if constexpr (MODE == 2) {
+        substep_mixed(c, cf, p, dt, s, xe_gf, td_gf, td64);
       } else {
-        substep_mixed(c, cf, p, dt, s, xe_gf, td_gf, td64, nullptr);
+#ifdef __CUDACC__
+        bool last;
+        const double dts = substep_start64(c, p, dt, s, (MODE == 3) ? td64 : td_g, last);
+        double seed[3];
+        const bool ok = mlp_seed(wsm, buf0, buf1, blockDim.x, lf, s, dts, p, seed);
+        if constexpr (MODE == 3) substep_mixed_solve(c, cf, p, dt, dts, last, s, xe_gf, td_gf, td64, ok ? seed : nullptr);
+        else solve_substep64(c, p, dt, dts, last, s, xe_g, td_g, ok ? seed : nullptr);
+#endif
       }
       if (!finite3(s.Tmu, s.xH2, s.xHp)) {
         s.status |= ST_NONFIN;

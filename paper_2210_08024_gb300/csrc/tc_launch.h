@@ -12,4 +12,11 @@ cudaError_t launch_mode1(bool batch, const DevFields& f, const BoxTable* d_boxes
                          unsigned long long* cursor, long long ntotal, int grid, int block, cudaStream_t st);
 cudaError_t launch_mode2(bool batch, const DevFields& f, const BoxTable* d_boxes, const DevParams& p, double dt,
                          unsigned long long* cursor, long long ntotal, int grid, int block, cudaStream_t st);
+// Seeded modes (3: mixed, 4: FP64 Newton); mlp points to the device weight blob.
+cudaError_t launch_mode3(bool batch, const DevFields& f, const BoxTable* d_boxes, const DevParams& p, double dt,
+                         unsigned long long* cursor, long long ntotal, int grid, int block, cudaStream_t st,
+                         const MlpDev* mlp);
+cudaError_t launch_mode4(bool batch, const DevFields& f, const BoxTable* d_boxes, const DevParams& p, double dt,
+                         unsigned long long* cursor, long long ntotal, int grid, int block, cudaStream_t st,
+                         const MlpDev* mlp);
 }  // namespace tcg

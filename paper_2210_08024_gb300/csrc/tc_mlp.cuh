@@ -1,0 +1,86 @@
+// Seed network of the implicit solve: layout of its weights on the device and the
+// per-lane inference used inside the step kernel.
+//
+// The network maps a cell's state, fields and step length (9 features) through three
+// hidden layers of 64 SiLU units to 3 outputs:
+//   o0 ~ x_H2(t+dt) / 0.5,  o1 ~ x_H+(t+dt),  o2 ~ log10 T(t+dt) - log10 T(t).
+// Features: log10 n, log10 T, x_H2, x_H+, log10 chi_FUV, log10 f_shld,H2,
+// log10(F_LyC + 1), log10 xi_cr, log10 dt; each normalised as (f - mean) * inv_std.
+// Weights are BF16, everything else FP32; sums accumulate in FP32.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tcg {
+
+constexpr int MLP_IN = 9, MLP_HID = 64, MLP_OUT = 3;
+constexpr int MLP_INP = 16;   // padded input width of W1
+constexpr uint32_t MLP_MAGIC = 0x4C4D4354u;  // "TCML"
+constexpr uint32_t MLP_VERSION = 1u;
+
+// Weights are stored transposed ([in][out]) so that one input's weights for 16
+// consecutive outputs are contiguous (two 16-byte loads, broadcast to the warp).
+struct MlpDev {
+  uint32_t magic, version, n_in, n_hid, n_out, bytes, pad0, pad1;
+  float in_mean[MLP_INP];
+  float in_inv_std[MLP_INP];
+  __nv_bfloat16 W1t[MLP_INP * MLP_HID];   // [k][j], rows k >= 9 zero
+  __nv_bfloat16 W2t[MLP_HID * MLP_HID];   // [k][j]
+  __nv_bfloat16 W3t[MLP_HID * MLP_HID];   // [k][j]
+  __nv_bfloat16 W4t[MLP_HID * 4];         // [k][m], column 3 zero
+  float b1[MLP_HID], b2[MLP_HID], b3[MLP_HID], b4[4];
+};
+static_assert(sizeof(MlpDev) % 16 == 0, "MlpDev must stay 16-byte sized");
+
+__device__ __forceinline__ float mlp_silu(float z) { return z / (1.0f + __expf(-z)); }
+
+// One hidden layer for this thread: out[j] = silu(b[j] + sum_k Wt[k][j] in[k]), with
+// in and out in shared memory at stride `st` (one column per thread of the block).
+template <int K>
+__device__ __forceinline__ void mlp_layer(const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ b,
+                                          const float* in, float* out, int st) {
+#pragma unroll 1
+  for (int j0 = 0; j0 < MLP_HID; j0 += 16) {
+    float acc[16];
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) acc[jj] = b[j0 + jj];
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+      const float a = in[k * st];
+      const __nv_bfloat162* w2 = reinterpret_cast<const __nv_bfloat162*>(Wt + k * MLP_HID + j0);
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const float2 w = __bfloat1622float2(w2[jj]);
+        acc[2 * jj] = fmaf(w.x, a, acc[2 * jj]);
+        acc[2 * jj + 1] = fmaf(w.y, a, acc[2 * jj + 1]);
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) out[(j0 + jj) * st] = mlp_silu(acc[jj]);
+  }
+}
+
+// Network output for raw features f[9].  `w` points to the weights in shared memory;
+// buf0/buf1 point to this thread's column of two [64][st] float buffers.
+__device__ __forceinline__ void mlp_infer(const MlpDev* w, float* buf0, float* buf1, int st, const float* f,
+                                          float* o) {
+#pragma unroll
+  for (int k = 0; k < MLP_IN; ++k) buf1[k * st] = (f[k] - w->in_mean[k]) * w->in_inv_std[k];
+  mlp_layer<MLP_IN>(w->W1t, w->b1, buf1, buf0, st);
+  mlp_layer<MLP_HID>(w->W2t, w->b2, buf0, buf1, st);
+  mlp_layer<MLP_HID>(w->W3t, w->b3, buf1, buf0, st);
+  float a0 = w->b4[0], a1 = w->b4[1], a2 = w->b4[2];
+#pragma unroll 8
+  for (int k = 0; k < MLP_HID; ++k) {
+    const float h = buf0[k * st];
+    a0 = fmaf(__bfloat162float(w->W4t[k * 4 + 0]), h, a0);
+    a1 = fmaf(__bfloat162float(w->W4t[k * 4 + 1]), h, a1);
+    a2 = fmaf(__bfloat162float(w->W4t[k * 4 + 2]), h, a2);
+  }
+  o[0] = a0;
+  o[1] = a1;
+  o[2] = a2;
+}
+
+}  // namespace tcg

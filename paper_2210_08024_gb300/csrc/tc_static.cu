@@ -126,6 +126,7 @@ extern "C" int tc_step_host_static(const tc_params* p, const tc_fields* f, doubl
   d.T = dst[0]; d.xH2 = dst[1]; d.xHp = dst[2]; d.xe = dst[3]; d.xCp = dst[4]; d.xCO = dst[5];
   d.nsub = f->nsub ? ibase : nullptr;
   d.status = f->status ? ibase + M : nullptr;
+  d.iters = nullptr;
   d.ncell = f->ncell;
   d.Zg_val = f->Zg_val;
   d.Zd_val = f->Zd_val;

@@ -52,6 +52,7 @@ class tc_fields(ctypes.Structure):
         ("nsub", _P), ("status", _P),
         ("ncell", ctypes.c_longlong),
         ("Zg_val", ctypes.c_double), ("Zd_val", ctypes.c_double),
+        ("newton_iters", _P),
     ]
 
 
@@ -59,7 +60,7 @@ class tc_fields(ctypes.Structure):
 FIELD_KEYS = {
     "n": "n", "chi_pe": "chi_pe", "chi_lw": "chi_lw", "f_shld_h2": "f_h2", "f_shld_c": "f_c", "F_lyc": "F_lyc",
     "xi_cr": "xi", "Zg": "Zg", "Zd": "Zd", "T": "T", "x_h2": "xH2", "x_hp": "xHp", "x_e": "xe", "x_cp": "xCp",
-    "x_co": "xCO", "nsub": "nsub", "status": "status",
+    "x_co": "xCO", "nsub": "nsub", "status": "status", "newton_iters": "iters",
 }
 
 
@@ -87,6 +88,21 @@ def _load():
     L.tc_peak_chains.restype = ctypes.c_int
     L.tc_step_host_static.argtypes = [ctypes.POINTER(tc_params), ctypes.POINTER(tc_fields), ctypes.c_double,
                                       ctypes.c_void_p]
+    # seed network (include/tc_mlp.h)
+    L.tc_mlp_n_params.restype = ctypes.c_int
+    L.tc_mlp_create.argtypes = [ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_void_p)]
+    L.tc_mlp_destroy.argtypes = [ctypes.c_void_p]
+    L.tc_mlp_destroy.restype = None
+    L.tc_mlp_set_norm.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.tc_mlp_set_params.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.tc_mlp_get_params.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.tc_mlp_predict.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    L.tc_mlp_grad.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.tc_mlp_train_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]
+    L.tc_mlp_blob_bytes.restype = ctypes.c_size_t
+    L.tc_mlp_export.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
     return L
 
 
@@ -230,7 +246,7 @@ def tc_peak_chains() -> int:
 
 
 # ----------------------------------------------------------------------------- helpers
-STATE_OUT = ("T", "xH2", "xHp", "xe", "xCp", "xCO", "nsub", "status")
+STATE_OUT = ("T", "xH2", "xHp", "xe", "xCp", "xCO", "nsub", "status", "iters")
 INPUT_KEYS = ("n", "chi_pe", "chi_lw", "f_h2", "f_c", "F_lyc", "xi", "Zg", "Zd")
 
 
@@ -249,7 +265,7 @@ def to_device(cells: dict, device="cuda", outputs: bool = True) -> dict:
     if outputs:
         for k in ("xe", "xCp", "xCO"):
             d[k] = torch.zeros(n, dtype=torch.float64, device=device)
-        for k in ("nsub", "status"):
+        for k in ("nsub", "status", "iters"):
             d[k] = torch.zeros(n, dtype=torch.int32, device=device)
     return d
 
@@ -300,3 +316,76 @@ def step_numpy(cells: dict, dt: float, mode: int = TC_MODE_PAPER_FP64, **params)
     out = from_device(d)
     st.close()
     return out
+
+
+# ----------------------------------------------------------------------------- seed network
+def _f32(a):
+    import numpy as np
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+class SeedNet:
+    """Handle of the seed network (include/tc_mlp.h).  X, Y are device float32 torch
+    tensors of shape [B, 9] and [B, 3]; all arithmetic runs in the library's kernels."""
+
+    def __init__(self, seed: int = 0):
+        self.h = ctypes.c_void_p()
+        _check(lib.tc_mlp_create(ctypes.c_ulonglong(seed), ctypes.byref(self.h)), "tc_mlp_create")
+
+    @staticmethod
+    def n_params() -> int:
+        return int(lib.tc_mlp_n_params())
+
+    def set_norm(self, mean, std) -> None:
+        m, s = _f32(mean), _f32(std)
+        _check(lib.tc_mlp_set_norm(self.h, m.ctypes.data, s.ctypes.data), "tc_mlp_set_norm")
+
+    def set_params(self, theta) -> None:
+        t = _f32(theta)
+        assert t.size == self.n_params()
+        _check(lib.tc_mlp_set_params(self.h, t.ctypes.data), "tc_mlp_set_params")
+
+    def get_params(self):
+        import numpy as np
+        t = np.zeros(self.n_params(), dtype=np.float32)
+        _check(lib.tc_mlp_get_params(self.h, t.ctypes.data), "tc_mlp_get_params")
+        return t
+
+    def predict(self, X, stream=None):
+        import torch
+        out = torch.empty((X.shape[0], 3), dtype=torch.float32, device=X.device)
+        _check(lib.tc_mlp_predict(self.h, X.data_ptr(), X.shape[0], out.data_ptr(), _stream_ptr(stream)),
+               "tc_mlp_predict")
+        return out
+
+    def grad(self, X, Y, w=(1.0, 1.0, 1.0), stream=None):
+        import torch
+        g = torch.empty(self.n_params(), dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        w3 = _f32(w)
+        _check(lib.tc_mlp_grad(self.h, X.data_ptr(), Y.data_ptr(), X.shape[0], w3.ctypes.data, g.data_ptr(),
+                               loss.data_ptr(), _stream_ptr(stream)), "tc_mlp_grad")
+        return g, loss
+
+    def train_step(self, X, Y, lr, loss_out=None, w=(1.0, 1.0, 1.0), stream=None) -> None:
+        w3 = _f32(w)
+        _check(lib.tc_mlp_train_step(self.h, X.data_ptr(), Y.data_ptr(), X.shape[0], w3.ctypes.data,
+                                     ctypes.c_float(lr), loss_out.data_ptr() if loss_out is not None else None,
+                                     _stream_ptr(stream)), "tc_mlp_train_step")
+
+    def export(self) -> bytes:
+        n = int(lib.tc_mlp_blob_bytes())
+        buf = ctypes.create_string_buffer(n)
+        _check(lib.tc_mlp_export(self.h, buf, n), "tc_mlp_export")
+        return buf.raw
+
+    def close(self) -> None:
+        if self.h:
+            lib.tc_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -22,7 +22,7 @@ def tc():
 
 def _declared():
     names = set()
-    for h in ("tc.h", "tc_peak.h"):
+    for h in sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")):
         src = open(os.path.join(ROOT, "include", h)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         for m in re.finditer(r"^\s*(?:const\s+)?[a-z_]+\s*\**\s*(tc_[a-z_0-9]+)\s*\(", src, flags=re.M):

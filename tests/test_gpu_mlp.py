@@ -1,0 +1,162 @@
+"""The seed network on the GPU: forward pass and gradients against the CPU FP64
+reference (oracle/mlp.py, same BF16-rounded weights), training, the weight blob, and
+the seeded step modes: the same results as the unseeded solver (root uniqueness) with
+fewer Newton iterations."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synthgen
+from oracle import mlp as ref_mlp
+from tests._parity import assert_fp64_parity, assert_mixed_parity
+
+pytestmark = pytest.mark.gpu
+
+DT = synthgen.DT_1E4YR
+
+
+@pytest.fixture(scope="module")
+def tc():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2210_08024_gb300 as P
+    P.build()
+    from paper_2210_08024_gb300 import tc as T
+    return T
+
+
+def _rounded(theta):
+    """The weights the kernels use: BF16-rounded weights, FP32 biases."""
+    parts = ref_mlp.unflatten(theta)
+    out = []
+    for i, p in enumerate(parts):
+        out.append(ref_mlp.bf16_round(p) if i % 2 == 0 else np.asarray(p, dtype=np.float32).astype(np.float64))
+    return ref_mlp.flatten(out)
+
+
+def _random_net(tc, seed=0):
+    g = np.random.default_rng(seed)
+    theta = (g.normal(0.0, 0.25, ref_mlp.n_params())).astype(np.float32)
+    net = tc.SeedNet(1)
+    net.set_params(theta)
+    net.set_norm(np.zeros(9), np.ones(9))
+    return net, theta.astype(np.float64)
+
+
+def test_forward_matches_fp64_reference(tc):
+    import torch
+    net, theta = _random_net(tc)
+    x = np.random.default_rng(1).normal(0, 1, (1000, 9)).astype(np.float32)
+    o = net.predict(torch.from_numpy(x).cuda()).cpu().numpy()
+    r, _, _ = ref_mlp.forward(_rounded(theta), x.astype(np.float64))
+    np.testing.assert_allclose(o, r, rtol=1e-4, atol=1e-5)
+    net.close()
+
+
+def test_gradient_matches_fp64_reference(tc):
+    import torch
+    net, theta = _random_net(tc, 2)
+    g = np.random.default_rng(3)
+    x = g.normal(0, 1, (4096, 9)).astype(np.float32)
+    y = g.normal(0, 1, (4096, 3)).astype(np.float32)
+    w = (1.0, 2.0, 0.5)
+    grad, loss = net.grad(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), w)
+    grad = grad.cpu().numpy().astype(np.float64)
+    th = _rounded(theta)
+    gr = ref_mlp.grad(th, x.astype(np.float64), y.astype(np.float64), w)
+    lr = ref_mlp.loss(th, x.astype(np.float64), y.astype(np.float64), w)
+    assert float(loss.item()) == pytest.approx(lr, rel=1e-4)
+    # whole-vector and per-block relative errors, FP32 accumulation over 4096 samples
+    assert np.linalg.norm(grad - gr) <= 1e-4 * np.linalg.norm(gr)
+    k = 0
+    for s in ref_mlp.SHAPES:
+        m = int(np.prod(s))
+        a, b = grad[k:k + m], gr[k:k + m]
+        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b) + 1e-9, s
+        k += m
+    net.close()
+
+
+def test_training_reduces_loss(tc):
+    import torch
+    g = np.random.default_rng(4)
+    x = g.normal(0, 1, (16384, 9)).astype(np.float32)
+    y = np.stack([np.tanh(x[:, 0] - x[:, 1]), 0.5 * x[:, 2] * x[:, 3], np.sin(x[:, 4])], axis=1).astype(np.float32)
+    net = tc.SeedNet(5)
+    X, Y = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    _, l0 = net.grad(X, Y)
+    loss = torch.zeros(1, device="cuda")
+    for i in range(300):
+        idx = torch.randint(0, 16384, (1024,), device="cuda")
+        net.train_step(X[idx], Y[idx], 3e-3, loss)
+    _, l1 = net.grad(X, Y)
+    assert float(l1.item()) < 0.1 * float(l0.item())
+    net.close()
+
+
+def test_blob_roundtrip_and_validation(tc):
+    net, _ = _random_net(tc, 6)
+    blob = net.export()
+    assert len(blob) == int(tc.lib.tc_mlp_blob_bytes())
+    st = tc.Stepper(tc.TC_MODE_MIXED_SEEDED)
+    st.load_mlp(blob)
+    with pytest.raises(tc.TcError):
+        st.load_mlp(blob[:-16])
+    bad = bytearray(blob)
+    bad[0] ^= 0xFF
+    with pytest.raises(tc.TcError):
+        st.load_mlp(bytes(bad))
+    st.close()
+    s2 = tc.Stepper(tc.TC_MODE_NEWTON_FP64_SEEDED)
+    d = tc.to_device(synthgen.cells_4096(n=64, key=8))
+    with pytest.raises(tc.TcError):   # seeded mode without weights
+        s2.step(d, DT)
+    s2.close()
+    net.close()
+
+
+@pytest.fixture(scope="module")
+def trained_blob(tc):
+    from paper_2210_08024_gb300 import seed_net
+    if os.path.exists(seed_net.DEFAULT_BLOB):
+        return open(seed_net.DEFAULT_BLOB, "rb").read()
+    X, Y, _, _ = seed_net.make_dataset(300_000, key=40, log=lambda *a: None)
+    net, _ = seed_net.train(X, Y, epochs=3, batch=4096, log=lambda *a: None)
+    blob = net.export()
+    net.close()
+    return blob
+
+
+def _run(tc, cells, mode, blob=None):
+    import torch
+    d = tc.to_device(cells)
+    st = tc.Stepper(mode)
+    if blob is not None:
+        st.load_mlp(blob)
+    st.step(d, DT)
+    torch.cuda.synchronize()
+    out = tc.from_device(d)
+    st.close()
+    return out
+
+
+def test_seeded_fp64_same_root_fewer_iterations(tc, trained_blob):
+    c = synthgen.slab(ncell=20000, key=41)
+    plain = _run(tc, c, tc.TC_MODE_NEWTON_FP64)
+    seeded = _run(tc, c, tc.TC_MODE_NEWTON_FP64_SEEDED, trained_blob)
+    assert np.all((seeded["status"] & tc.TC_ST_ERROR_MASK) == 0)
+    assert_fp64_parity(seeded, plain, "seeded-vs-plain")
+    ref = oracle.step(synthgen.subset(c, slice(0, 2000)), DT, oracle.default_params(mode=1))
+    assert_fp64_parity(synthgen.subset(seeded, slice(0, 2000)), ref, "seeded-vs-oracle")
+    print("Newton iterations per cell: plain %.3f, seeded %.3f" % (plain["iters"].mean(), seeded["iters"].mean()))
+    assert seeded["iters"].sum() < plain["iters"].sum()
+
+
+def test_seeded_mixed_within_tolerance(tc, trained_blob):
+    c = synthgen.cells_4096(n=4096, key=42)
+    ref = oracle.step(c, DT, oracle.default_params(mode=1))
+    g = _run(tc, c, tc.TC_MODE_MIXED_SEEDED, trained_blob)
+    assert np.all((g["status"] & tc.TC_ST_ERROR_MASK) == 0)
+    assert_mixed_parity(g, ref, "mixed-seeded")
