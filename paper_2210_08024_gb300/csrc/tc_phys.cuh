@@ -346,7 +346,9 @@ template <class F> TCG_FN Equil<F> equilibrium(const CellC<F>& c, const ChemT<F>
       if (g > F(0)) hi = x; else lo = x;
       F gp = F(1) - w * d;
       F xn = x - g / gp;
-      if (!(xn > lo && xn < hi)) xn = F(0.5) * (lo + hi);
+      // a Newton step that lands on a bracket end is kept: near the root the bracket
+      // collapses onto it, and bisecting there would only grind the bracket down
+      if (!(xn >= lo && xn <= hi)) xn = F(0.5) * (lo + hi);
       F dx = m_abs(xn - x);
       x = xn;
       xe = x;
@@ -387,7 +389,7 @@ template <class F> TCG_FN F dust_T(const CellC<F>& c, F T, F sqT, F guess) {
     if (h > F(0)) hi = y; else lo = y;
     F dh = c.Bd * y * (F(6) * y2 * y2 - F(2) * c.Tc4) + C;
     F yn = y - h / dh;
-    if (!(yn > lo && yn < hi)) yn = F(0.5) * (lo + hi);
+    if (!(yn >= lo && yn <= hi)) yn = F(0.5) * (lo + hi);  // bracket ends allowed, as above
     F dy = m_abs(yn - y);
     y = yn;
     if (dy <= tol * y || hi - lo <= tol * hi) break;
