@@ -12,7 +12,8 @@
  *   features: log10 n, log10 T, x_H2, x_H+, log10 chi_FUV, log10 f_shld,H2,
  *             log10(F_LyC + 1), log10 xi_cr, log10 dt   (raw; normalised inside with the
  *             mean and standard deviation given to tc_mlp_set_norm)
- *   outputs:  x_H2(t+dt)/0.5, x_H+(t+dt), log10 T(t+dt) - log10 T(t)
+ *   outputs:  changes over one backward-Euler step of length dt (the implicit solve's
+ *             root): (x_H2' - x_H2)/0.5, x_H+' - x_H+, log10 T' - log10 T
  * Parameters: one FP32 master vector of tc_mlp_n_params() floats, in the order
  *   W1[64][9], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[3][64], b4[3].
  * The forward and backward passes use the weights rounded to BF16 and accumulate in

@@ -237,8 +237,9 @@ TCG_FN bool damped_step(double* y, const double* d, double* st) {
 // floored at 1e-17), converged when every full step is below rtol |y_i|.
 // Returns iterations used, or -1.
 TCG_FN int newton_solve(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
-                        double dts, double* y, double& xe_g, double& td_g) {
-  for (int it = 1; it <= p.newton_max; ++it) {
+                        double dts, double* y, double& xe_g, double& td_g, int maxit = 0) {
+  const int nmax = (maxit > 0 && maxit < p.newton_max) ? maxit : p.newton_max;
+  for (int it = 1; it <= nmax; ++it) {
     double f0[3], J[3][3];
     ChemT<double> b = chem_T(c, mu * y[0], p.flags);
     CoolT<double> k = cool_T(c, b, p.flags);
@@ -316,6 +317,10 @@ TCG_FN void finish_substep(const CellC<F>& cf, double muH, const DevParams& p, d
   s.t = last ? dt : s.t + dts;
 }
 
+// A seeded Newton solve that has not converged after this many iterations is abandoned
+// and the substep restarts from its start state: a poor seed then costs little.
+constexpr int SEED_MAXIT = 6;
+
 // Solves one substep of length dts by the FP64 Newton iteration, from `seed` when
 // given (the root is the same; a seeded solve that fails is retried from the start
 // state), else from the start state; a failed solve is retried at half length (up to
@@ -328,8 +333,9 @@ TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double d
   int it = -1;
   if (seed) {
     y[0] = seed[0]; y[1] = seed[1]; y[2] = seed[2];
-    it = newton_solve(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g);
-    if (it < 0) { y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2]; }
+    double xg = xe_g, tg = td_g;
+    it = newton_solve(c, p, s.mu, Kinv, yn, dts, y, xg, tg, SEED_MAXIT);
+    if (it < 0) { y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2]; } else { xe_g = xg; td_g = tg; }
   }
   if (it < 0) it = newton_solve(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g);
   int halv = 0;
@@ -497,6 +503,11 @@ TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<float>& cf, 
   double J[3][3];
   bool polish = false;
   int it = newton_mixed(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, J, polish);
+  if (it < 0 && seed) {
+    // a seed that did not lead to convergence: start again from the start state
+    y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2];
+    it = newton_mixed(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, J, polish);
+  }
   if (it >= 0) {
     if (polish) s.status |= ST_POLISH;
     double xg = double(xe_g), tg = double(td_g);
@@ -522,7 +533,6 @@ TCG_FN void substep_mixed(const CellC<double>& c, const CellC<float>& cf, const 
 }
 
 // ------------------------------------------------------------------ seeding (modes 3, 4)
-#ifdef __CUDACC__
 // Shared-memory footprint of the seeded kernels for `block` threads: the weights and
 // two [64][block] activation buffers.
 __host__ __device__ constexpr size_t seed_smem_bytes(int block) {
@@ -531,26 +541,27 @@ __host__ __device__ constexpr size_t seed_smem_bytes(int block) {
 
 // Seed of a substep's Newton iteration from the network: features of the substep start
 // (state, per-cell field features lf[5] = log10 n, log10 chi_FUV, log10 f_shld,H2,
-// log10(F_LyC+1), log10 xi) and its length; outputs mapped to (T_mu, x_H2, x_H+) with
-// mu frozen at the substep start and clamped inside the admissible region.  Returns
+// log10(F_LyC+1), log10 xi) and its length; the outputs are the predicted changes of
+// x_H2 (/0.5), x_H+ and log10 T over the substep's backward-Euler step, mapped to
+// (T_mu, x_H2, x_H+) with mu frozen at the substep start and clamped inside the
+// admissible region.  Returns
 // false (no seed) if the prediction is not finite.
-__device__ __forceinline__ bool mlp_seed(const MlpDev* w, float* buf0, float* buf1, int st, const float* lf,
-                                         const LaneState& s, double dts, const DevParams& p, double* seed) {
+TCG_FN bool mlp_seed(const MlpDev* w, float* buf0, float* buf1, int st, const float* lf, const LaneState& s,
+                     double dts, const DevParams& p, double* seed) {
   const double T0 = s.mu * s.Tmu;
   float f[MLP_IN] = {lf[0], (float)log10(T0), (float)s.xH2, (float)s.xHp, lf[1], lf[2], lf[3], lf[4],
                      (float)log10(dts)};
   float o[MLP_OUT];
   mlp_infer(w, buf0, buf1, st, f, o);
   if (!(isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]))) return false;
-  const double x2 = fmin(fmax(0.5 * (double)o[0], 1e-20), 0.4999999);
-  const double xp = fmin(fmax((double)o[1], 1e-20), 0.999999 * (1.0 - 2.0 * x2));
+  const double x2 = fmin(fmax(s.xH2 + 0.5 * (double)o[0], 1e-20), 0.4999999);
+  const double xp = fmin(fmax(s.xHp + (double)o[1], 1e-20), 0.999999 * (1.0 - 2.0 * x2));
   const double T1 = fmin(fmax(T0 * exp10((double)fmin(fmax(o[2], -6.f), 6.f)), p.T_floor), 1e10);
   seed[0] = T1 / s.mu;
   seed[1] = x2;
   seed[2] = xp;
   return true;
 }
-#endif
 
 // ------------------------------------------------------------------ the kernel
 template <int MODE, bool BATCH>
@@ -646,14 +657,12 @@ __global__ void __launch_bounds__(128) k_step(DevFields f1, const BoxTable* __re
       } else if constexpr (MODE == 2) {
         substep_mixed(c, cf, p, dt, s, xe_gf, td_gf, td64);
       } else {
-#ifdef __CUDACC__
         bool last;
         const double dts = substep_start64(c, p, dt, s, (MODE == 3) ? td64 : td_g, last);
         double seed[3];
         const bool ok = mlp_seed(wsm, buf0, buf1, blockDim.x, lf, s, dts, p, seed);
         if constexpr (MODE == 3) substep_mixed_solve(c, cf, p, dt, dts, last, s, xe_gf, td_gf, td64, ok ? seed : nullptr);
         else solve_substep64(c, p, dt, dts, last, s, xe_g, td_g, ok ? seed : nullptr);
-#endif
       }
       if (!finite3(s.Tmu, s.xH2, s.xHp)) {
         s.status |= ST_NONFIN;

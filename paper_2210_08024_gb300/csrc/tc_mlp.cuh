@@ -2,14 +2,16 @@
 // per-lane inference used inside the step kernel.
 //
 // The network maps a cell's state, fields and step length (9 features) through three
-// hidden layers of 64 SiLU units to 3 outputs:
-//   o0 ~ x_H2(t+dt) / 0.5,  o1 ~ x_H+(t+dt),  o2 ~ log10 T(t+dt) - log10 T(t).
+// hidden layers of 64 SiLU units to 3 outputs, the changes over one backward-Euler
+// step of length dt (the root the implicit solve looks for):
+//   o0 ~ (x_H2' - x_H2) / 0.5,  o1 ~ x_H+' - x_H+,  o2 ~ log10 T' - log10 T.
 // Features: log10 n, log10 T, x_H2, x_H+, log10 chi_FUV, log10 f_shld,H2,
 // log10(F_LyC + 1), log10 xi_cr, log10 dt; each normalised as (f - mean) * inv_std.
 // Weights are BF16, everything else FP32; sums accumulate in FP32.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 namespace tcg {
@@ -33,12 +35,22 @@ struct MlpDev {
 };
 static_assert(sizeof(MlpDev) % 16 == 0, "MlpDev must stay 16-byte sized");
 
-__device__ __forceinline__ float mlp_silu(float z) { return z / (1.0f + __expf(-z)); }
+// Inference is host+device so that the host build of the step functions can run the
+// seeded modes too.
+#define TCG_MLP_FN __host__ __device__ __forceinline__
+
+TCG_MLP_FN float mlp_silu(float z) {
+#ifdef __CUDA_ARCH__
+  return z / (1.0f + __expf(-z));
+#else
+  return z / (1.0f + expf(-z));
+#endif
+}
 
 // One hidden layer for this thread: out[j] = silu(b[j] + sum_k Wt[k][j] in[k]), with
 // in and out in shared memory at stride `st` (one column per thread of the block).
 template <int K>
-__device__ __forceinline__ void mlp_layer(const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ b,
+TCG_MLP_FN void mlp_layer(const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ b,
                                           const float* in, float* out, int st) {
 #pragma unroll 1
   for (int j0 = 0; j0 < MLP_HID; j0 += 16) {
@@ -63,7 +75,7 @@ __device__ __forceinline__ void mlp_layer(const __nv_bfloat16* __restrict__ Wt, 
 
 // Network output for raw features f[9].  `w` points to the weights in shared memory;
 // buf0/buf1 point to this thread's column of two [64][st] float buffers.
-__device__ __forceinline__ void mlp_infer(const MlpDev* w, float* buf0, float* buf1, int st, const float* f,
+TCG_MLP_FN void mlp_infer(const MlpDev* w, float* buf0, float* buf1, int st, const float* f,
                                           float* o) {
 #pragma unroll
   for (int k = 0; k < MLP_IN; ++k) buf1[k * st] = (f[k] - w->in_mean[k]) * w->in_inv_std[k];

@@ -1,15 +1,17 @@
 """Training data, training loop and export of the seed network.
 
-The network (include/tc_mlp.h) predicts a cell's state at the end of a step of length
-dt from its state, fields and dt.  The seeded step modes start each substep's Newton
-iteration from that prediction and still iterate to the solver's own tolerance, so the
-prediction only shortens the iteration.
+The network (include/tc_mlp.h) predicts the root of one backward-Euler step of length
+dt, as changes from the cell's state, from its state, fields and dt.  The seeded step
+modes start each substep's Newton iteration from that prediction and still iterate to
+the solver's own tolerance, so the prediction only shortens the iteration.
 
 Training data: cells drawn like the 128^3 slab (synthgen.training_samples: lognormal
 density, two-phase temperatures, six-ray fields) with Z' log-uniform in [0.1, 3] and
-dt log-uniform in [1e-3, 1] x 1e4 yr.  Labels come from the library's plain FP64 solver
-(TC_MODE_NEWTON_FP64, checked against the CPU oracle by the parity tests).  Each sample's
-dt is rounded to one of `nbins` log-spaced values so that a bin is one tc_step call.
+step lengths log-uniform in [1e-6, 1] x 1e4 yr, wide enough to cover the substeps that
+the 0.1 limiter produces.  Labels come from the library's plain FP64 solver
+(TC_MODE_NEWTON_FP64, checked against the CPU oracle by the parity tests) run with the
+substep limiter switched off, so each label is a single backward-Euler root.  Each
+sample's step length is one of `nbins` log-spaced values so that a bin is one tc_step.
 Training: Adam on mini-batches with the library's forward/backward kernels
 (tc_mlp_train_step); everything numerical runs on the GPU in those kernels.
 
@@ -55,48 +57,61 @@ def features(cells: dict, T, xH2, xHp, dt) -> np.ndarray:
     return X
 
 
-def targets(T0, T1, xH2_1, xHp_1) -> np.ndarray:
-    """x_H2(t+dt)/0.5, x_H+(t+dt), log10 T(t+dt) - log10 T(t), float32 [N, 3]."""
+def targets(T0, xH2_0, xHp_0, xe0, T1, xH2_1, xHp_1, xe1) -> np.ndarray:
+    """Changes over one backward-Euler step, float32 [N, 3]: (x_H2' - x_H2)/0.5,
+    x_H+' - x_H+ and log10 T' - log10 T, where T' = mu_0 T_mu' is the root's temperature
+    at the step's start mu (the frozen mu of the residual).  The solver returns
+    T1 = mu_1 T_mu', so T' = T1 mu_0 / mu_1 with mu = mu_H / (1.1 + x_e - x_H2)."""
+    ratio = (1.1 + np.asarray(xe1) - np.asarray(xH2_1)) / (1.1 + np.asarray(xe0) - np.asarray(xH2_0))
     Y = np.empty((np.size(T0), 3), dtype=np.float32)
-    Y[:, 0] = np.asarray(xH2_1) / 0.5
-    Y[:, 1] = np.asarray(xHp_1)
-    Y[:, 2] = np.log10(np.asarray(T1)) - np.log10(np.asarray(T0))
+    Y[:, 0] = (np.asarray(xH2_1) - np.asarray(xH2_0)) / 0.5
+    Y[:, 1] = np.asarray(xHp_1) - np.asarray(xHp_0)
+    Y[:, 2] = np.log10(np.asarray(T1) * ratio) - np.log10(np.asarray(T0))
     return Y
 
 
-def make_dataset(n: int, key: int = 4, nbins: int = 32, mode: int = tc.TC_MODE_NEWTON_FP64, log=print):
-    """Returns (X, Y, cells, dt) with labels from the GPU FP64 solver."""
+def make_dataset(n: int, key: int = 4, nbins: int = 48, dt_range=(1e-6, 1.0), log=print):
+    """Returns (X, Y, cells, dt).  Labels: one backward-Euler step of length dt per sample
+    (the substep rule switched off by a huge limiter), solved by the library's plain FP64
+    Newton; samples whose solve needed a halved substep are dropped."""
     import torch
     cells = synthgen.training_samples(n, key)
-    dt = cells.pop("dt")
-    lo, hi = math.log10(synthgen.DT_1E4YR * 1e-3), math.log10(synthgen.DT_1E4YR)
+    cells.pop("dt")
+    g = np.random.default_rng(key + 1)
+    lo, hi = math.log10(synthgen.DT_1E4YR * dt_range[0]), math.log10(synthgen.DT_1E4YR * dt_range[1])
     edges = np.linspace(lo, hi, nbins + 1)
-    b = np.clip(np.digitize(np.log10(dt), edges) - 1, 0, nbins - 1)
+    b = g.integers(0, nbins, n)
     centers = 10.0 ** (0.5 * (edges[:-1] + edges[1:]))
     dt = centers[b]
-    st = tc.Stepper(mode)
-    T1 = np.empty(n)
-    x21 = np.empty(n)
-    xp1 = np.empty(n)
+    st0 = tc.Stepper(tc.TC_MODE_NEWTON_FP64)
+    st1 = tc.Stepper(tc.TC_MODE_NEWTON_FP64, limiter=1e30)
+    out = {k: np.empty(n) for k in ("xe0", "T1", "x21", "xp1", "xe1")}
+    nsub = np.empty(n, dtype=np.int32)
     t0 = time.time()
     for k in range(nbins):
         idx = np.nonzero(b == k)[0]
         if idx.size == 0:
             continue
-        d = tc.to_device(synthgen.subset(cells, idx))
-        st.step(d, float(centers[k]))
+        sub = synthgen.subset(cells, idx)
+        d = tc.to_device(sub)
+        st0.step(d, 0.0)                 # dt = 0: the initial C/O/e equilibrium only
         torch.cuda.synchronize()
-        bad = tc.tc_sync_status(st.h, d["status"])
-        if bad:
-            log("  bin %d: %d cells with status bits" % (k, bad))
-        T1[idx] = d["T"].cpu().numpy()
-        x21[idx] = d["xH2"].cpu().numpy()
-        xp1[idx] = d["xHp"].cpu().numpy()
-    st.close()
-    log("labels for %d samples in %.1f s" % (n, time.time() - t0))
+        out["xe0"][idx] = d["xe"].cpu().numpy()
+        d = tc.to_device(sub)
+        st1.step(d, float(centers[k]))
+        torch.cuda.synchronize()
+        out["T1"][idx] = d["T"].cpu().numpy()
+        out["x21"][idx] = d["xH2"].cpu().numpy()
+        out["xp1"][idx] = d["xHp"].cpu().numpy()
+        out["xe1"][idx] = d["xe"].cpu().numpy()
+        nsub[idx] = d["nsub"].cpu().numpy()
+    st0.close()
+    st1.close()
+    log("labels for %d samples in %.1f s (%d needed more than one substep)" % (n, time.time() - t0,
+                                                                           int(np.sum(nsub != 1))))
     X = features(cells, cells["T"], cells["xH2"], cells["xHp"], dt)
-    Y = targets(cells["T"], T1, x21, xp1)
-    ok = np.all(np.isfinite(X), axis=1) & np.all(np.isfinite(Y), axis=1)
+    Y = targets(cells["T"], cells["xH2"], cells["xHp"], out["xe0"], out["T1"], out["x21"], out["xp1"], out["xe1"])
+    ok = np.all(np.isfinite(X), axis=1) & np.all(np.isfinite(Y), axis=1) & (nsub == 1)
     return X[ok], Y[ok], synthgen.subset(cells, np.nonzero(ok)[0]), dt[ok]
 
 
