@@ -320,6 +320,8 @@ TCG_FN void finish_substep(const CellC<F>& cf, double muH, const DevParams& p, d
 // A seeded Newton solve that has not converged after this many iterations is abandoned
 // and the substep restarts from its start state: a poor seed then costs little.
 constexpr int SEED_MAXIT = 6;
+// Largest predicted changes (log10 T, abundances) for which a seed is used.
+constexpr float SEED_MAX_DLOGT = 0.02f, SEED_MAX_DX = 0.02f;
 
 // Solves one substep of length dts by the FP64 Newton iteration, from `seed` when
 // given (the root is the same; a seeded solve that fails is retried from the start
@@ -554,6 +556,10 @@ TCG_FN bool mlp_seed(const MlpDev* w, float* buf0, float* buf1, int st, const fl
   float o[MLP_OUT];
   mlp_infer(w, buf0, buf1, st, f, o);
   if (!(isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]))) return false;
+  // Trust region: the backward-Euler system can have several roots (thermally unstable
+  // gas), and the solver's root is the one Newton reaches from the start state.  A seed
+  // is used only when it predicts a small change, inside the basin of that root.
+  if (fabsf(o[2]) > SEED_MAX_DLOGT || fabsf(0.5f * o[0]) > SEED_MAX_DX || fabsf(o[1]) > SEED_MAX_DX) return false;
   const double x2 = fmin(fmax(s.xH2 + 0.5 * (double)o[0], 1e-20), 0.4999999);
   const double xp = fmin(fmax(s.xHp + (double)o[1], 1e-20), 0.999999 * (1.0 - 2.0 * x2));
   const double T1 = fmin(fmax(T0 * exp10((double)fmin(fmax(o[2], -6.f), 6.f)), p.T_floor), 1e10);
