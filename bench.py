@@ -43,6 +43,9 @@ UNIT = "cell-updates/s"
 FP64_NOMINAL_TFLOPS = 1.25
 
 STATE_KEYS = ("T", "xH2", "xHp")
+# DRAM bytes per cell of one k_step<1> launch, from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum on a 112^3 slab, profiles/k_step_fp64_slab128.md), scaled by cells.
+TRAFFIC_BYTES_PER_CELL = 138.9
 
 
 def parse():
@@ -67,10 +70,16 @@ def dist_env():
     return ws, rank, local
 
 
-def opcount_per_cell():
-    path = os.path.join(ROOT, "tests", "golden", "opcount_slab128.json")
+def work_per_cell():
+    """FP64 operations per cell by class (add, mul, div, sqrt, exp, log) of one step on
+    the slab, per mode, counted from the library's own step functions
+    (paper_2210_08024_gb300/work.py)."""
+    path = os.path.join(ROOT, "paper_2210_08024_gb300", "work_slab128.json")
     with open(path) as fh:
-        return json.load(fh)
+        return json.load(fh)["per_cell"]
+
+
+MODE_WORK = {"paper": "mode0", "newton": "mode1", "mixed": "mode2", "newton_seeded": "mode1", "mixed_seeded": "mode2"}
 
 
 class ClockSampler:
@@ -152,8 +161,10 @@ def measure_peaks(tc, torch):
     return {"fp64_fma_per_s": fma, "fp32_fma_per_s": rates["fma32"], "rates": rates, "weights": weights}
 
 
-def slots_per_cell(counts: dict, weights: dict) -> float:
-    return sum(counts[k] * weights[k] for k in ("add", "mul", "div", "sqrt", "exp", "log", "pow"))
+def flops_per_cell(counts: dict, weights: dict) -> float:
+    """FP64 work in FMA-equivalent flops: an add or a multiply is 1 flop; a divide,
+    sqrt, exp or log costs its measured number of FMA slots at 2 flops per slot."""
+    return counts["add"] + counts["mul"] + 2.0 * sum(counts[k] * weights[k] for k in ("div", "sqrt", "exp", "log"))
 
 
 def run_gpu(args):
@@ -292,14 +303,18 @@ def run_e2e(args, tc, torch, cells, ncell, mode_id, stream, barrier, ws):
 
 
 def report(args, results, head, ncell, peaks, e2e, clocks, cells, ws):
-    # roofline of the step kernel (FP64 pipe): algorithmic FP64 work per launch from the
-    # oracle's operation counts per cell, weighted by the measured FMA-slot cost of each
-    # operation class, over the CUDA-event duration of the launch.
-    oc = opcount_per_cell()
+    # roofline of the step kernel (FP64 pipe): the FP64 work of one launch (per-cell
+    # counts of the library's own step, weighted by the FMA-slot cost of each operation
+    # class measured in this run) over the CUDA-event duration of the launch.
+    work = work_per_cell()
     r = results[head]
     roofline = None
     if peaks is not None:
-        roofline = roofline_of(oc, r, head, ncell, peaks)
+        roofline = roofline_of(work, r, head, ncell, peaks)
+        for name, rr in results.items():
+            rl = roofline_of(work, rr, name, ncell, peaks)
+            rr["fp64_roofline_frac"] = rl["frac"]
+            rr["fp64_tflops"] = rl["achieved"]
     cpu = None if args.no_cpu_baseline else cpu_baseline(cells, head)
     out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
@@ -320,17 +335,18 @@ def report(args, results, head, ncell, peaks, e2e, clocks, cells, ws):
     return out
 
 
-def roofline_of(oc, r, head, ncell, peaks):
-    counts = oc["mode%d" % (0 if head == "paper" else 1)]
-    slots = slots_per_cell(counts, peaks["weights"]) * ncell
-    achieved = 2.0 * slots / (r["kernel_ms"] * 1e-3) / 1e12
+def roofline_of(work, r, mode, ncell, peaks):
+    fl = flops_per_cell(work[MODE_WORK[mode]], peaks["weights"]) * ncell
+    achieved = fl / (r["kernel_ms"] * 1e-3) / 1e12
     peak = 2.0 * peaks["fp64_fma_per_s"] / 1e12
     return {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "measured FP64 FMA rate (library microbenchmark, this run); nominal %.2f" %
-                               FP64_NOMINAL_TFLOPS,
-                "work": "oracle op count per cell x %d cells, FMA-slot weights measured" % ncell,
-                "kernel": "k_step<%d,false>" % (0 if head == "paper" else 1)}
+            "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_CELL * ncell if mode == "newton" else None,
+            "peak_source": "measured FP64 FMA rate (library microbenchmark, this run); nominal %.2f" %
+                           FP64_NOMINAL_TFLOPS,
+            "work": "FP64 flops of the library's step per cell (work_slab128.json, %s) x %d cells" %
+                    (MODE_WORK[mode], ncell),
+            "kernel": "k_step<%d,false>" % {"paper": 0, "newton": 1, "mixed": 2, "mixed_seeded": 3,
+                                             "newton_seeded": 4}[mode]}
 
 
 def oracle_sample(cells, head, budget_s=15.0):

@@ -100,6 +100,7 @@ TCG_FN double substep_len(const DevParams& p, double rem, double e, double H, do
 
 // ------------------------------------------------------------------ mode 0: paper scheme
 TCG_FN void substep_paper(const CellC<double>& c, const DevParams& p, double dt, LaneState& s) {
+  TCG_COUNT_D(substep_paper);
   const double T = s.mu * s.Tmu;
   const double e = c.K * s.Tmu;
   double H0 = 0.0, CH2 = 0.0, CHp = 0.0, Td0 = -1.0, Hp = 0.0;
@@ -240,6 +241,7 @@ TCG_FN int newton_solve(const CellC<double>& c, const DevParams& p, double mu, d
                         double dts, double* y, double& xe_g, double& td_g, int maxit = 0) {
   const int nmax = (maxit > 0 && maxit < p.newton_max) ? maxit : p.newton_max;
   for (int it = 1; it <= nmax; ++it) {
+    TCG_COUNT_D(newton64_it);
     double f0[3], J[3][3];
     ChemT<double> b = chem_T(c, mu * y[0], p.flags);
     CoolT<double> k = cool_T(c, b, p.flags);
@@ -405,6 +407,7 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
   double prev = 1e300;
   polish = false;
   for (int it = 1; it <= p.newton_max; ++it) {
+    TCG_COUNT_D(newton32_it);
     ChemT<float> b = chem_T(cf, float(mu * y[0]), p.flags);
     CoolT<float> k = cool_T(cf, b, p.flags);
     double f0[3];
@@ -469,6 +472,7 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
 TCG_FN bool polish64(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
                      double dts, double* y, const double J[3][3], double& xe_g, double& td_g) {
   for (int it = 0; it < 3; ++it) {
+    TCG_COUNT_D(polish_it);
     ChemT<double> b = chem_T(c, mu * y[0], p.flags);
     CoolT<double> k = cool_T(c, b, p.flags);
     double f0[3];

@@ -22,6 +22,15 @@
 #ifndef TCG_FN
 #define TCG_FN __host__ __device__ __forceinline__
 #endif
+// Work-counting hooks: empty in the library; the host work counter (tc_workcount.cu)
+// defines them to count calls and inner iterations of the step's building blocks.
+// TCG_COUNT is used inside templates on the scalar type F; TCG_COUNT_D in FP64 code.
+#ifndef TCG_COUNT
+#define TCG_COUNT(name)
+#endif
+#ifndef TCG_COUNT_D
+#define TCG_COUNT_D(name)
+#endif
 
 namespace tcg {
 
@@ -174,6 +183,7 @@ template <class F> struct ChemT {
 };
 
 template <class F> TCG_FN ChemT<F> chem_T(const CellC<F>& c, F T, unsigned flags) {
+  TCG_COUNT(chem_T);
   ChemT<F> b;
   b.T = T;
   b.lnT = m_log(T);
@@ -223,6 +233,7 @@ template <class F> struct CoolT {
 };
 
 template <class F> TCG_FN CoolT<F> cool_T(const CellC<F>& c, const ChemT<F>& b, unsigned flags) {
+  TCG_COUNT(cool_T);
   CoolT<F> k;
   const F T = b.T, lnT = b.lnT;
   F invT = F(1) / T;
@@ -303,6 +314,7 @@ template <class F> struct Equil {
 // at `guess`, to a relative step of 1e-14 (FP64) / 1e-7 (FP32).
 template <class F> TCG_FN Equil<F> equilibrium(const CellC<F>& c, const ChemT<F>& b, F xH2,
                                                                   F xHp, F guess) {
+  TCG_COUNT(equil);
   Equil<F> q;
   const F w = F(1) - b.S;
   q.xOp = c.xOtot * xHp;
@@ -340,6 +352,7 @@ template <class F> TCG_FN Equil<F> equilibrium(const CellC<F>& c, const ChemT<F>
     const F tol = (sizeof(F) == 8) ? F(1e-14) : F(1e-7);
     xe = x;
     for (int it = 0; it < 100; ++it) {
+      TCG_COUNT(equil_it);
       F d;
       F g = x - a0 - w * xcp(x, d);
       if (g == F(0)) { xe = x; break; }
@@ -374,6 +387,7 @@ template <class F> TCG_FN Equil<F> equilibrium(const CellC<F>& c, const ChemT<F>
 // the bracket midpoint instead would take ~70 linearly convergent steps in hot gas.
 template <class F> TCG_FN F dust_T(const CellC<F>& c, F T, F sqT, F guess) {
   if (!(c.Zd > F(0))) return T;
+  TCG_COUNT(dust);
   F C = c.Cgd * sqT;
   F lo = m_min(T, c.Tc);
   F hi = m_max(m_max(T, F(1.2) * c.Tc), c.Td_hi);
@@ -384,6 +398,7 @@ template <class F> TCG_FN F dust_T(const CellC<F>& c, F T, F sqT, F guess) {
   }
   const F tol = (sizeof(F) == 8) ? F(1e-14) : F(1e-7);
   for (int it = 0; it < 100; ++it) {
+    TCG_COUNT(dust_it);
     F y2 = y * y;
     F h = c.Bd * y2 * (y2 * y2 - c.Tc4) - c.Gd - C * (T - y);
     if (h > F(0)) hi = y; else lo = y;
@@ -443,6 +458,7 @@ template <class F> struct Src {
 template <class F> TCG_FN Src<F> source(const CellC<F>& c, const ChemT<F>& b, const CoolT<F>& k,
                                                             F xH2, F xHp, F xH, const Equil<F>& q, F Td_fixed,
                                                             F Td_guess) {
+  TCG_COUNT(source);
   Src<F> s;
   const F n = c.n;
   const F xe = q.xe;

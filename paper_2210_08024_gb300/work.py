@@ -1,0 +1,99 @@
+"""FP64 work per cell of the library's step, for the roofline of the benchmark.
+
+Builds and runs csrc/tc_workcount.cu, a host build of the library's own step
+functions with counting hooks.  It writes work_slab128.json: for each mode, the FP64
+operations per cell by class (add, mul, div, sqrt, exp, log) of one step of dt = 1e4 yr
+on a seeded sample of the 128^3 slab.  bench.py weights them by the FMA-slot cost of
+each class, measured in the same run, to state the work one launch performs.
+
+The dense 3x3 linear algebra of each Newton iteration (FD-Jacobian differencing, the
+residual, Gaussian elimination, damping and convergence test) is not templated on the
+scalar type; its counts per iteration are stated here from the code:
+    FP64 Newton iteration   60 add, 55 mul, 19 div
+    mixed Newton iteration  45 add, 35 mul, 17 div   (its FP64 part)
+    FP64 polish iteration   36 add, 31 mul, 13 div
+    paper-scheme substep    18 add, 18 mul,  8 div   (FD slope, T update, 2x2 solve)
+
+    python -m paper_2210_08024_gb300.work
+"""
+from __future__ import annotations
+
+import json
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+OUT = os.path.join(HERE, "work_slab128.json")
+LINALG = {
+    "newton64_it": {"add": 60, "mul": 55, "div": 19},
+    "newton32_it": {"add": 45, "mul": 35, "div": 17},
+    "polish_it": {"add": 36, "mul": 31, "div": 13},
+    "substep_paper": {"add": 18, "mul": 18, "div": 8},
+}
+CLASSES = ("add", "mul", "div", "sqrt", "exp", "log")
+BLOCKS = {"chem_T": "cost_chem_T", "cool_T": "cost_cool_T", "source": "cost_source", "equil": "cost_equil_setup",
+          "equil_it": "cost_equil_iter", "dust": "cost_dust_setup", "dust_it": "cost_dust_iter"}
+
+
+def build(tmp: str) -> str:
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    exe = os.path.join(tmp, "tc_workcount")
+    cmd = [nvcc, "-std=c++17", "-O2", "-x", "cu", "-gencode", "arch=compute_103a,code=sm_103a",
+           os.path.join(HERE, "csrc", "tc_workcount.cu"), "-o", exe]
+    subprocess.run(cmd, check=True, capture_output=True)
+    return exe
+
+
+def per_cell(counts: dict) -> dict:
+    """FP64 operations per cell by class for each mode."""
+    out = {}
+    for mode in ("mode0", "mode1", "mode2"):
+        calls = counts[mode]["fp64"]
+        tot = {c: 0.0 for c in CLASSES}
+        for blk, key in BLOCKS.items():
+            for c in CLASSES:
+                tot[c] += calls[blk] * counts[key][c]
+        for blk, la in LINALG.items():
+            for c, v in la.items():
+                tot[c] += calls[blk] * v
+        out[mode] = {c: round(v, 2) for c, v in tot.items()}
+        out[mode]["substeps"] = counts[mode]["substeps"]
+    return out
+
+
+def main(sample: int = 8192):
+    import synthgen
+    c = synthgen.slab()
+    idx = np.sort(np.random.default_rng(12345).choice(c["n"].size, sample, replace=False))
+    sub = synthgen.subset(c, idx)
+    keys = ("n", "chi_pe", "chi_lw", "f_h2", "f_c", "F_lyc", "xi", "Zg", "Zd", "T", "xH2", "xHp")
+    with tempfile.TemporaryDirectory() as tmp:
+        exe = build(tmp)
+        path = os.path.join(tmp, "cells.bin")
+        with open(path, "wb") as fh:
+            fh.write(np.int64(sample).tobytes())
+            for k in keys:
+                fh.write(np.ascontiguousarray(np.broadcast_to(np.asarray(sub[k], np.float64), (sample,))).tobytes())
+            fh.write(np.float64(synthgen.DT_1E4YR).tobytes())
+        r = subprocess.run([exe, path], check=True, capture_output=True, text=True)
+    counts = json.loads(r.stdout)
+    res = {"_comment": "FP64 operations per cell of one step (dt = 1e4 yr) on %d seeded cells of the 128^3 slab, "
+                       "counted from the library's own step functions (paper_2210_08024_gb300/work.py)." % sample,
+           "per_cell": per_cell(counts), "raw": counts}
+    with open(OUT, "w") as fh:
+        json.dump(res, fh, indent=1)
+    print(OUT)
+    return res
+
+
+if __name__ == "__main__":
+    main()

@@ -1,7 +1,7 @@
 """The seed network on the GPU: forward pass and gradients against the CPU FP64
 reference (oracle/mlp.py, same BF16-rounded weights), training, the weight blob, and
-the seeded step modes: the same results as the unseeded solver (root uniqueness) with
-fewer Newton iterations."""
+the seeded step modes: the same roots as the unseeded solver, with the Newton
+iteration counts reported."""
 import os
 
 import numpy as np
