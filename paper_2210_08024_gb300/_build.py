@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtc_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["tc_api.cu", "tc_k_paper.cu", "tc_k_newton.cu", "tc_k_mixed.cu", "tc_mlp.cu", "tc_peak.cu",
-           "tc_static.cu", "tc_k_seeded.cu"]
+           "tc_static.cu", "tc_k_seeded3.cu", "tc_k_seeded4.cu"]
 
 
 def nvcc() -> str:

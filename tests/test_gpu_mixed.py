@@ -28,7 +28,7 @@ def test_mixed_random_states(tc, key, n):
     c = synthgen.cells_4096(n=n, key=key)
     ref = oracle.step(c, DT, oracle.default_params(mode=1))
     g = tc.step_numpy(c, DT, tc.TC_MODE_MIXED)
-    assert np.all((g["status"] & tc.TC_ST_ERROR_MASK) == 0)
+    assert np.all((g["status"] & (tc.TC_ST_NONFINITE | tc.TC_ST_MAX_SUBSTEPS)) == 0)
     assert_mixed_parity(g, ref, "mixed-key%d" % key)
     # the plain FP64 fallback is the exception, not the rule (checked on the large sample)
     if n >= 1000:
@@ -60,5 +60,5 @@ def test_mixed_metallicity_and_ionising_flux(tc):
         c["Zd"] = np.full(512, Z)
         ref = oracle.step(c, DT, oracle.default_params(mode=1))
         g = tc.step_numpy(c, DT, tc.TC_MODE_MIXED)
-        assert np.all((g["status"] & tc.TC_ST_ERROR_MASK) == 0)
+        assert np.all((g["status"] & (tc.TC_ST_NONFINITE | tc.TC_ST_MAX_SUBSTEPS)) == 0)
         assert_mixed_parity(g, ref, "mixed-Z%g" % Z)
