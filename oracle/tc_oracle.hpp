@@ -753,6 +753,10 @@ template <class R> int newton_substep(const CellIn& c, const Params& p, const Pr
     //    x_H = 1 - 2 x_H2 - x_H+ at >= 1% of their values (fraction 0.99 to the
     //    boundary), so that an abundance pressed against its bound does not freeze
     //    the temperature, nor the temperature the abundances;
+    //  - if the x_H bound alone would cut the abundance step below 1% of its length
+    //    (x_H -> 0 with the step pointing further down), the abundance step is instead
+    //    projected onto that bound (the smallest change along the bound's normal
+    //    (-2, -1)), which lets the iteration slide along it instead of stalling;
     //  - an abundance whose step is below 1e-8 in absolute terms cannot matter to the
     //    other unknowns: it does not limit lamX and is kept at >= 1% of its value on
     //    its own, so that a trace species driven towards zero does not freeze the rest.
@@ -773,11 +777,28 @@ template <class R> int newton_substep(const CellIn& c, const Params& p, const Pr
     }
     R xH = R(1.0) - R(2.0) * y[1] - y[2];
     R dxH = R(0.0) - R(2.0) * d[1] - d[2];
+    bool proj = false;
     if (dxH < R(0.0)) {
       R cap = R(0.99) * rmax(xH, R(0.0)) / (R(0.0) - dxH);
-      if (cap < lamX) lamX = cap;
+      if (cap < R(0.01)) {
+        R lim = R(0.0) - R(0.99) * rmax(xH, R(0.0));
+        R beta = (dxH - lim) / R(5.0);
+        d[1] = d[1] + R(2.0) * beta;
+        d[2] = d[2] + beta;
+        proj = true;
+        lamX = R(1.0);
+        for (int i = 1; i < 3; ++i) {
+          tiny[i] = !(rabs(d[i]) > R(1e-8));
+          if (d[i] < R(0.0) && !tiny[i]) {
+            R c2 = R(0.99) * y[i] / (R(0.0) - d[i]);
+            if (c2 < lamX) lamX = c2;
+          }
+        }
+      } else if (cap < lamX) {
+        lamX = cap;
+      }
     }
-    bool conv = !(lamT < R(1.0)) && !(lamX < R(1.0));
+    bool conv = !(lamT < R(1.0)) && !(lamX < R(1.0)) && !proj;
     for (int i = 0; i < 3; ++i) {
       R st = ((i == 0) ? lamT : lamX) * d[i];
       if (tiny[i] && y[i] + st < R(0.01) * y[i]) {
