@@ -204,10 +204,13 @@ TCG_FN bool solve3(double J[3][3], double b[3], double d[3]) {
 // Damping of a Newton step d, by blocks (the root is unchanged, only the path to it):
 // T_mu takes the step length lamT that keeps it at >= 1% of its value; x_H2 and x_H+
 // share a length lamX that keeps them and x_H = 1 - 2 x_H2 - x_H+ at >= 1% of their
-// values (fraction 0.99 to the boundary), so that neither block freezes the other.  An
-// abundance whose step is below 1e-8 in absolute terms does not limit lamX and is kept
-// at >= 1% of its value on its own.  Applies the step to y, writes the steps taken to
-// st and returns true if no limit acted (a full Newton step).
+// values (fraction 0.99 to the boundary), so that neither block freezes the other.  If
+// the x_H bound alone would cut the abundance step below 1% of its length, the step is
+// projected onto that bound instead (the smallest change along its normal (-2, -1)),
+// so the iteration slides along it rather than stalling.  An abundance whose step is
+// below 1e-8 in absolute terms does not limit lamX and is kept at >= 1% of its value on
+// its own.  Applies the step to y, writes the steps taken to st and returns true if no
+// limit acted (a full Newton step).
 TCG_FN bool damped_step(double* y, const double* d, double* st) {
   double lamT = 1.0, lamX = 1.0;
   if (d[0] < 0.0) lamT = fmin(lamT, 0.99 * y[0] / (-d[0]));
@@ -218,10 +221,29 @@ TCG_FN bool damped_step(double* y, const double* d, double* st) {
   }
   const double xH = 1.0 - 2.0 * y[1] - y[2];
   const double dxH = -2.0 * d[1] - d[2];
-  if (dxH < 0.0) lamX = fmin(lamX, 0.99 * fmax(xH, 0.0) / (-dxH));
-  bool full = !(lamT < 1.0) && !(lamX < 1.0);
+  bool proj = false;
+  double e1 = d[1], e2 = d[2];
+  if (dxH < 0.0) {
+    const double cap = 0.99 * fmax(xH, 0.0) / (-dxH);
+    if (cap < 0.01) {
+      const double lim = -0.99 * fmax(xH, 0.0);
+      const double beta = (dxH - lim) / 5.0;
+      e1 += 2.0 * beta;
+      e2 += beta;
+      proj = true;
+      lamX = 1.0;
+      tiny[1] = !(fabs(e1) > 1e-8);
+      tiny[2] = !(fabs(e2) > 1e-8);
+      if (e1 < 0.0 && !tiny[1]) lamX = fmin(lamX, 0.99 * y[1] / (-e1));
+      if (e2 < 0.0 && !tiny[2]) lamX = fmin(lamX, 0.99 * y[2] / (-e2));
+    } else {
+      lamX = fmin(lamX, cap);
+    }
+  }
+  const double dd[3] = {d[0], e1, e2};
+  bool full = !(lamT < 1.0) && !(lamX < 1.0) && !proj;
   for (int i = 0; i < 3; ++i) {
-    double s = ((i == 0) ? lamT : lamX) * d[i];
+    double s = ((i == 0) ? lamT : lamX) * dd[i];
     if (tiny[i] && y[i] + s < 0.01 * y[i]) {
       s = -0.99 * y[i];
       full = false;
