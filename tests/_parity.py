@@ -15,6 +15,13 @@ to ~1e-9.  The mode-0 bound therefore adds four times that measured one-ulp spre
 (``ulp_spread``) to the 1e-9 relative bound, cell by cell.
 
 Mixed path vs the FP64 oracle: 1e-5 relative on T and 1e-6 absolute on abundances.
+
+The coupled scheme (mode 1) halves a substep whose Newton solve fails.  Whether the
+solve of a given substep fails can hinge on the last bit of the state, and in rare
+cells (hot gas cooling through 1e4 K over many substeps) the two branches end ~1e-4
+apart in T: the oracle itself, given one input abundance one unit in the last place
+away, lands on the other branch.  Tests on such workloads add four times the oracle's
+spread over one-ulp changes of T, x_H2 and x_H+ (``ulp_spread(..., inputs=...)``).
 """
 import numpy as np
 
@@ -31,18 +38,19 @@ def rel_err(a, b, floor=0.0):
     return np.abs(a - b) / np.maximum(np.abs(b), floor)
 
 
-def ulp_spread(oracle_mod, cells, dt, params):
-    """Largest change of the oracle's outputs when every input temperature moves by
-    one unit in the last place (up or down): a per-cell measure of how much rounding
-    the scheme amplifies."""
+def ulp_spread(oracle_mod, cells, dt, params, inputs=("T",)):
+    """Largest change of the oracle's outputs when one input state variable (each of
+    `inputs` in turn) moves by one unit in the last place (up or down): a per-cell
+    measure of how much rounding the scheme amplifies."""
     base = oracle_mod.step(cells, dt, params)
     spread = {k: np.zeros_like(base[k]) for k in ("T", "xH2", "xHp")}
-    for direction in (np.inf, 0.0):
-        c2 = dict(cells)
-        c2["T"] = np.nextafter(np.asarray(cells["T"], dtype=np.float64), direction)
-        r2 = oracle_mod.step(c2, dt, params)
-        for k in spread:
-            spread[k] = np.maximum(spread[k], np.abs(r2[k] - base[k]))
+    for key in inputs:
+        for direction in (np.inf, 0.0):
+            c2 = dict(cells)
+            c2[key] = np.nextafter(np.asarray(cells[key], dtype=np.float64), direction)
+            r2 = oracle_mod.step(c2, dt, params)
+            for k in spread:
+                spread[k] = np.maximum(spread[k], np.abs(r2[k] - base[k]))
     return base, spread
 
 
@@ -61,9 +69,14 @@ def assert_fp64_parity(gpu, ref, label="", spread=None):
             label, k, bad.size, np.nanmax(err / np.maximum(np.abs(b), 1e-300)), bad[0], a[bad[0]], b[bad[0]])
 
 
-def assert_mixed_parity(gpu, ref, label=""):
-    eT = rel_err(gpu["T"], ref["T"])
-    assert np.all(eT <= RTOL_T_MIXED), "%s T: max rel %.3e" % (label, np.nanmax(eT))
+def assert_mixed_parity(gpu, ref, label="", spread=None):
+    b = np.asarray(ref["T"], dtype=np.float64)
+    err = np.abs(np.asarray(gpu["T"], dtype=np.float64) - b)
+    tol = RTOL_T_MIXED * np.abs(b)
+    if spread is not None:
+        tol = tol + SPREAD_FACTOR * spread["T"]
+    assert np.all(err <= tol), "%s T: max rel %.3e" % (label, np.nanmax(err / np.abs(b)))
     for k in ("xH2", "xHp"):
         ea = np.abs(np.asarray(gpu[k]) - np.asarray(ref[k]))
-        assert np.all(ea <= ATOL_X_MIXED), "%s %s: max abs %.3e" % (label, k, np.nanmax(ea))
+        tk = ATOL_X_MIXED + (SPREAD_FACTOR * spread[k] if spread is not None else 0.0)
+        assert np.all(ea <= tk), "%s %s: max abs %.3e" % (label, k, np.nanmax(ea))
