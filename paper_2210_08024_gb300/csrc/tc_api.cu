@@ -12,7 +12,11 @@
 #include <new>
 
 #include "../../include/tc.h"
+#include "../../include/tc_onezone.h"
+#include "../../include/tc_pdr.h"
 #include "tc_launch.h"
+#include "tc_onezone.cuh"
+#include "tc_pdr.cuh"
 
 namespace tcg {
 int occupancy_mode0_impl(int block);
@@ -42,6 +46,12 @@ struct tc_handle {
   // MLP seed weights (device) -- loaded by tc_load_mlp
   void* d_mlp = nullptr;
   size_t mlp_bytes = 0;
+  // driver workspace (tc_eq_curves, tc_pdr): per-cell arrays and the parameter arrays
+  double* d_eq = nullptr;
+  int* d_eqi = nullptr;
+  size_t eq_cells = 0;
+  double* d_eqpar = nullptr;
+  size_t eqpar_len = 0;
 };
 
 extern "C" {
@@ -113,6 +123,9 @@ void tc_destroy(tc_handle* h) {
   cudaFree(h->d_buf);
   cudaFree(h->d_ibuf);
   cudaFree(h->d_mlp);
+  cudaFree(h->d_eq);
+  cudaFree(h->d_eqi);
+  cudaFree(h->d_eqpar);
   delete h;
 }
 
@@ -394,3 +407,228 @@ extern "C" int tc_sync_status(tc_handle* h, const int* status, long long ncell, 
   *nbad = (long long)v;
   return TC_OK;
 }
+
+// ----- driver workspace shared by the one-zone and PDR drivers
+// Grows the per-cell workspace (DRIVER_NW doubles and 2 ints per cell) and the
+// parameter buffer, waits for earlier work on the stream (it may still read the previous
+// call's parameters), copies the five host parameter arrays and waits for the copies.
+static const size_t DRIVER_NW = 11;
+
+static int driver_setup(tc_handle* h, size_t ncell, const double* const hp[5], const size_t len[5], double* dp[5],
+                        cudaStream_t st) {
+  if (h->eq_cells < ncell) {
+    cudaFree(h->d_eq);
+    cudaFree(h->d_eqi);
+    h->d_eq = nullptr;
+    h->d_eqi = nullptr;
+    h->eq_cells = 0;
+    if (cudaMalloc(&h->d_eq, ncell * DRIVER_NW * sizeof(double)) != cudaSuccess) return TC_ENOMEM;
+    if (cudaMalloc(&h->d_eqi, ncell * 2 * sizeof(int)) != cudaSuccess) return TC_ENOMEM;
+    h->eq_cells = ncell;
+  }
+  size_t npar = 0;
+  for (int k = 0; k < 5; ++k) npar += len[k];
+  if (h->eqpar_len < npar) {
+    cudaFree(h->d_eqpar);
+    h->d_eqpar = nullptr;
+    h->eqpar_len = 0;
+    if (cudaMalloc(&h->d_eqpar, npar * sizeof(double)) != cudaSuccess) return TC_ENOMEM;
+    h->eqpar_len = npar;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return TC_ECUDA;
+  size_t off = 0;
+  for (int k = 0; k < 5; ++k) {
+    dp[k] = h->d_eqpar + off;
+    if (cudaMemcpyAsync(dp[k], hp[k], len[k] * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return TC_ECUDA;
+    off += len[k];
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return TC_ECUDA;
+  return TC_OK;
+}
+
+static bool all_finite_nonneg(const double* a, long long n, bool positive) {
+  for (long long i = 0; i < n; ++i)
+    if (!isfinite(a[i]) || a[i] < 0.0 || (positive && !(a[i] > 0.0))) return false;
+  return true;
+}
+
+static bool start_state_ok(double T, double x2, double xp) {
+  return T > 0.0 && isfinite(T) && x2 >= 0.0 && xp >= 0.0 && 2.0 * x2 + xp <= 1.0;
+}
+
+// Step inputs of a driver run, laid out in the workspace.
+static tcg::DevFields driver_fields(tc_handle* h, size_t n, double* T, double* xH2, double* xHp, double* xe,
+                                    double* xCO) {
+  double* b = h->d_eq;
+  tcg::DevFields f;
+  memset(&f, 0, sizeof(f));
+  f.n = b; f.chi_pe = b + n; f.chi_lw = b + 2 * n; f.fh2 = b + 3 * n; f.xi = b + 4 * n;
+  f.Zg = b + 5 * n; f.Zd = b + 6 * n; f.chi0 = b + 7 * n;
+  f.fc = nullptr; f.Flyc = nullptr;
+  f.T = T; f.xH2 = xH2; f.xHp = xHp; f.xe = xe; f.xCp = nullptr; f.xCO = xCO;
+  f.nsub = nullptr; f.status = h->d_eqi; f.iters = nullptr;
+  f.ncell = (long long)n;
+  return f;
+}
+
+// ----- one-zone equilibrium curves (include/tc_onezone.h)
+extern "C" int tc_eq_spec_default(tc_eq_spec* s) {
+  if (!s) return TC_EINVAL;
+  memset(s, 0, sizeof(*s));
+  s->L_shld0_pc = 5.0;
+  s->n_shld0 = 1e2;
+  s->a_shld = 0.7;
+  s->t_end_s = 1e2 * 1e6 * 3.15576e7;
+  s->nchunk = 10;
+  s->T_init = 3000.0;
+  s->xH2_init = 0.0;
+  s->xHp_init = 1e-2;
+  return TC_OK;
+}
+
+extern "C" int tc_eq_curves(tc_handle* h, const tc_eq_spec* s, const tc_eq_out* o, void* stream) {
+  if (!h || !s || !o) return TC_EINVAL;
+  if (s->nn < 1 || s->ncurve < 1 || s->nchunk < 1 || !s->n_axis || !s->chi0 || !s->xi0 || !s->Zg || !s->Zd)
+    return TC_EINVAL;
+  if (!(s->t_end_s >= 0.0) || !isfinite(s->t_end_s)) return TC_EINVAL;
+  if (!all_finite_nonneg(s->n_axis, s->nn, true) || !all_finite_nonneg(s->chi0, s->ncurve, false) ||
+      !all_finite_nonneg(s->xi0, s->ncurve, false) || !all_finite_nonneg(s->Zg, s->ncurve, false) ||
+      !all_finite_nonneg(s->Zd, s->ncurve, false))
+    return TC_EINVAL;
+  if (s->shielded && !(s->L_shld0_pc >= 0.0 && s->n_shld0 > 0.0 && isfinite(s->a_shld))) return TC_EINVAL;
+  if (!start_state_ok(s->T_init, s->xH2_init, s->xHp_init)) return TC_EINVAL;
+  const void* req[] = {o->T, o->x_h2, o->x_hp, o->x_e, o->P_k};
+  for (const void* q : req)
+    if (!q || !aligned8(q)) return TC_EINVAL;
+  if ((o->x_co && !aligned8(o->x_co)) || (o->chg && !aligned8(o->chg))) return TC_EINVAL;
+  if (h->p.mode == TC_MODE_MIXED_SEEDED || h->p.mode == TC_MODE_NEWTON_FP64_SEEDED) {
+    if (!h->d_mlp) return TC_ENOMLP;
+  }
+  if ((double)s->nn * (double)s->ncurve > 9.0e15) return TC_EINVAL;
+  const long long ncell = s->nn * (long long)s->ncurve;
+  cudaStream_t st = (cudaStream_t)stream;
+  const double* hp[5] = {s->n_axis, s->chi0, s->xi0, s->Zg, s->Zd};
+  const size_t len[5] = {(size_t)s->nn, (size_t)s->ncurve, (size_t)s->ncurve, (size_t)s->ncurve, (size_t)s->ncurve};
+  double* dp[5];
+  int rc0 = driver_setup(h, (size_t)ncell, hp, len, dp, st);
+  if (rc0 != TC_OK) return rc0;
+
+  tcg::EqGrid g;
+  g.n_axis = dp[0]; g.chi0 = dp[1]; g.xi0 = dp[2]; g.Zg = dp[3]; g.Zd = dp[4];
+  g.nn = s->nn;
+  g.ncurve = s->ncurve;
+  g.shielded = s->shielded ? 1 : 0;
+  g.L0_cm = s->L_shld0_pc * 3.0856775814913673e18;
+  g.n0 = s->n_shld0;
+  g.a = s->a_shld;
+  g.T0 = s->T_init;
+  g.xH20 = s->xH2_init;
+  g.xHp0 = s->xHp_init;
+  const size_t n = (size_t)ncell;
+  tcg::DevFields f = driver_fields(h, n, o->T, o->x_h2, o->x_hp, o->x_e, o->x_co);
+  tcg::EqWork w;
+  w.n = const_cast<double*>(f.n); w.chi_pe = const_cast<double*>(f.chi_pe); w.chi_lw = const_cast<double*>(f.chi_lw);
+  w.fh2 = const_cast<double*>(f.fh2); w.xi = const_cast<double*>(f.xi); w.Zg = const_cast<double*>(f.Zg);
+  w.Zd = const_cast<double*>(f.Zd); w.chi0 = const_cast<double*>(f.chi0);
+  w.prev = h->d_eq + 8 * n;
+  w.st = h->d_eqi; w.st_acc = h->d_eqi + n;
+  const double dt = s->t_end_s / s->nchunk;
+  for (int k = 0; k < s->nchunk; ++k) {
+    if (tcg::launch_eq_fields(g, w, o->T, o->x_h2, o->x_hp, k, k == s->nchunk - 1, st) != cudaSuccess)
+      return TC_ECUDA;
+    h->launches += 1;
+    int rc = enqueue(h, false, f, ncell, dt, st);
+    if (rc != TC_OK) return rc;
+  }
+  if (tcg::launch_eq_finish(g, w, o->T, o->x_h2, o->x_hp, o->x_e, o->P_k, o->chg, o->status, st) != cudaSuccess)
+    return TC_ECUDA;
+  h->launches += 1;
+  if (o->i_max || o->i_min) {
+    if (tcg::launch_eq_extrema(g, o->P_k, o->i_max, o->i_min, st) != cudaSuccess) return TC_ECUDA;
+    h->launches += 1;
+  }
+  return TC_OK;
+}
+
+// ----- PDR slabs (include/tc_pdr.h)
+extern "C" int tc_pdr_spec_default(tc_pdr_spec* s) {
+  if (!s) return TC_EINVAL;
+  memset(s, 0, sizeof(*s));
+  s->t_end_s = 3e2 * 1e6 * 3.15576e7;
+  s->nchunk = 300;
+  s->T_init = 100.0;
+  s->xH2_init = 0.0;
+  s->xHp_init = 1e-4;
+  return TC_OK;
+}
+
+extern "C" int tc_pdr(tc_handle* h, const tc_pdr_spec* s, const tc_pdr_out* o, void* stream) {
+  if (!h || !s || !o) return TC_EINVAL;
+  if (s->nslab < 1 || s->ncell < 1 || s->nchunk < 1 || !s->n || !s->chi0 || !s->xi0 || !s->Z || !s->dx_cm)
+    return TC_EINVAL;
+  if (!(s->t_end_s >= 0.0) || !isfinite(s->t_end_s)) return TC_EINVAL;
+  if (!all_finite_nonneg(s->n, s->nslab, true) || !all_finite_nonneg(s->dx_cm, s->nslab, true) ||
+      !all_finite_nonneg(s->chi0, s->nslab, false) || !all_finite_nonneg(s->xi0, s->nslab, false) ||
+      !all_finite_nonneg(s->Z, s->nslab, false))
+    return TC_EINVAL;
+  if (!start_state_ok(s->T_init, s->xH2_init, s->xHp_init)) return TC_EINVAL;
+  const void* req[] = {o->T, o->x_h2, o->x_hp, o->x_e};
+  for (const void* q : req)
+    if (!q || !aligned8(q)) return TC_EINVAL;
+  const void* opt[] = {o->x_co, o->chi_pe, o->f_shld_h2, o->N_c, o->N_trans};
+  for (const void* q : opt)
+    if (q && !aligned8(q)) return TC_EINVAL;
+  if (h->p.mode == TC_MODE_MIXED_SEEDED || h->p.mode == TC_MODE_NEWTON_FP64_SEEDED) {
+    if (!h->d_mlp) return TC_ENOMLP;
+  }
+  if ((double)s->nslab * (double)s->ncell > 9.0e15) return TC_EINVAL;
+  const long long ncell = s->ncell * (long long)s->nslab;
+  cudaStream_t st = (cudaStream_t)stream;
+  const double* hp[5] = {s->n, s->chi0, s->xi0, s->Z, s->dx_cm};
+  const size_t ns = (size_t)s->nslab;
+  const size_t len[5] = {ns, ns, ns, ns, ns};
+  double* dp[5];
+  int rc0 = driver_setup(h, (size_t)ncell, hp, len, dp, st);
+  if (rc0 != TC_OK) return rc0;
+
+  tcg::PdrSlabs g;
+  g.n = dp[0]; g.chi0 = dp[1]; g.xi0 = dp[2]; g.Z = dp[3]; g.dx = dp[4];
+  g.nslab = s->nslab;
+  g.ncell = s->ncell;
+  g.T0 = s->T_init;
+  g.xH20 = s->xH2_init;
+  g.xHp0 = s->xHp_init;
+  const size_t n = (size_t)ncell;
+  tcg::DevFields f = driver_fields(h, n, o->T, o->x_h2, o->x_hp, o->x_e, o->x_co);
+  tcg::PdrWork w;
+  w.n = const_cast<double*>(f.n); w.chi_pe = const_cast<double*>(f.chi_pe); w.chi_lw = const_cast<double*>(f.chi_lw);
+  w.fh2 = const_cast<double*>(f.fh2); w.xi = const_cast<double*>(f.xi); w.Zg = const_cast<double*>(f.Zg);
+  w.Zd = const_cast<double*>(f.Zd); w.chi0 = const_cast<double*>(f.chi0);
+  w.st = h->d_eqi; w.st_acc = h->d_eqi + n;
+  const double dt = s->t_end_s / s->nchunk;
+  for (int k = 0; k < s->nchunk; ++k) {
+    if (tcg::launch_pdr_fields(g, w, o->T, o->x_h2, o->x_hp, k, false, nullptr, nullptr, nullptr, st) != cudaSuccess)
+      return TC_ECUDA;
+    h->launches += 1;
+    int rc = enqueue(h, false, f, ncell, dt, st);
+    if (rc != TC_OK) return rc;
+  }
+  if (tcg::launch_pdr_fields(g, w, o->T, o->x_h2, o->x_hp, s->nchunk, true, o->chi_pe, o->f_shld_h2, o->N_c, st) !=
+      cudaSuccess)
+    return TC_ECUDA;
+  h->launches += 1;
+  if (o->status) {
+    // the last launch's status OR-ed with the accumulated one
+    if (cudaMemcpyAsync(o->status, w.st, n * sizeof(int), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return TC_ECUDA;
+    if (tcg::launch_or_status(o->status, w.st_acc, ncell, st) != cudaSuccess) return TC_ECUDA;
+    h->launches += 1;
+  }
+  if (o->N_trans) {
+    if (tcg::launch_pdr_ntrans(g, o->x_h2, o->N_trans, st) != cudaSuccess) return TC_ECUDA;
+    h->launches += 1;
+  }
+  return TC_OK;
+}
+

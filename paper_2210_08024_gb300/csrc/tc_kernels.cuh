@@ -29,6 +29,7 @@ struct DevFields {
   int *nsub, *status, *iters;
   long long ncell;
   double Zg_val, Zd_val;
+  const double* chi0 = nullptr;   // optional per-cell unattenuated FUV scale (driver runs)
 };
 
 // Box table for batched launches: cells [start[b], start[b+1]) belong to box b.
@@ -64,7 +65,7 @@ TCG_FN void load_cell(const DevFields& f, long long i, const DevParams& p, CellC
   double Zd = f.Zd ? f.Zd[i] : f.Zd_val;
   double fc = f.fc ? f.fc[i] : 1.0;
   double Fl = f.Flyc ? f.Flyc[i] : 0.0;
-  c = make_cell(f.n[i], f.chi_pe[i], f.chi_lw[i], f.fh2[i], fc, Fl, f.xi[i], Zg, Zd, p);
+  c = make_cell(f.n[i], f.chi_pe[i], f.chi_lw[i], f.fh2[i], fc, Fl, f.xi[i], Zg, Zd, p, f.chi0 ? f.chi0[i] : -1.0);
   T0 = f.T[i];
   xH20 = f.xH2[i];
   xHp0 = f.xHp[i];

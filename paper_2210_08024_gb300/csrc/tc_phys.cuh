@@ -100,7 +100,10 @@ template <class F> struct CellC {
 // Builds the per-cell constants in FP64 (always), then converts.
 TCG_FN CellC<double> make_cell(double n, double chi_pe, double chi_lw, double fh2, double fc,
                                                    double Flyc, double xi, double Zg, double Zd,
-                                                   const DevParams& p) {
+                                                   const DevParams& p, double chi0_cell = -1.0) {
+  // chi0: the unattenuated FUV scale of the optical dust heating; per cell when given
+  // (driver runs with several radiation scales in one launch), else the launch's.
+  const double chi0 = (chi0_cell >= 0.0) ? chi0_cell : p.chi0;
   CellC<double> c;
   c.n = n;
   c.lnn = log(n);
@@ -133,10 +136,10 @@ TCG_FN CellC<double> make_cell(double n, double chi_pe, double chi_lw, double fh
   // dust heating: absorption of PE, LW (c E = 4 pi J) and LyC photons (Sec. 4.3.6 with
   // the Sec. 2.4 cross sections) and the attenuated optical band.
   double g = Zd * (FOURPI * (0.9e-21 * 1.8e-4 * chi_pe + 1.5e-21 * 3.0e-5 * chi_lw) + 1.9e-21 * 19.4 * EV * Flyc);
-  if (p.opt_over_fuv > 0.0 && p.chi0 > 0.0) {
-    double ratio = fmin(chi_pe / p.chi0, 1.0);
+  if (p.opt_over_fuv > 0.0 && chi0 > 0.0) {
+    double ratio = fmin(chi_pe / chi0, 1.0);
     double att = (ratio > 0.0) ? exp(p.tau_ratio * log(ratio)) : 0.0;
-    g += 0.3e-21 * Zd * p.opt_over_fuv * FOURPI * 2.1e-4 * p.chi0 * att;
+    g += 0.3e-21 * Zd * p.opt_over_fuv * FOURPI * 2.1e-4 * chi0 * att;
   }
   c.Gd = g;
   c.Bd = 2e-27 * Zd * CLIGHT * ARAD;

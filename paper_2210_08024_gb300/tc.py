@@ -64,6 +64,47 @@ FIELD_KEYS = {
 }
 
 
+class tc_eq_spec(ctypes.Structure):
+    """include/tc_onezone.h: the one-zone grid (host arrays) and integration settings."""
+    _fields_ = [
+        ("n_axis", ctypes.c_void_p), ("nn", ctypes.c_longlong),
+        ("chi0", ctypes.c_void_p), ("xi0", ctypes.c_void_p), ("Zg", ctypes.c_void_p), ("Zd", ctypes.c_void_p),
+        ("ncurve", ctypes.c_int), ("shielded", ctypes.c_int),
+        ("L_shld0_pc", ctypes.c_double), ("n_shld0", ctypes.c_double), ("a_shld", ctypes.c_double),
+        ("t_end_s", ctypes.c_double), ("nchunk", ctypes.c_int),
+        ("T_init", ctypes.c_double), ("xH2_init", ctypes.c_double), ("xHp_init", ctypes.c_double),
+    ]
+
+
+class tc_eq_out(ctypes.Structure):
+    """include/tc_onezone.h: device output arrays, curve-major."""
+    _fields_ = [(k, ctypes.c_void_p) for k in ("T", "x_h2", "x_hp", "x_e", "P_k", "x_co", "chg", "status",
+                                                "i_max", "i_min")]
+
+
+class tc_pdr_spec(ctypes.Structure):
+    """include/tc_pdr.h: per-slab parameters (host arrays) and integration settings."""
+    _fields_ = [
+        ("n", ctypes.c_void_p), ("chi0", ctypes.c_void_p), ("xi0", ctypes.c_void_p), ("Z", ctypes.c_void_p),
+        ("dx_cm", ctypes.c_void_p), ("nslab", ctypes.c_int), ("ncell", ctypes.c_longlong),
+        ("t_end_s", ctypes.c_double), ("nchunk", ctypes.c_int),
+        ("T_init", ctypes.c_double), ("xH2_init", ctypes.c_double), ("xHp_init", ctypes.c_double),
+    ]
+
+
+class tc_pdr_out(ctypes.Structure):
+    """include/tc_pdr.h: device outputs, slab-major."""
+    _fields_ = [(k, ctypes.c_void_p) for k in ("T", "x_h2", "x_hp", "x_e", "x_co", "chi_pe", "f_shld_h2", "N_c",
+                                                "status", "N_trans")]
+
+
+class tc_sixray_grid(ctypes.Structure):
+    """include/tc_sixray.h: grid shape, cell size and the unattenuated fields."""
+    _fields_ = [("nx", ctypes.c_longlong), ("ny", ctypes.c_longlong), ("nz", ctypes.c_longlong),
+                ("dx_cm", ctypes.c_double), ("chi0", ctypes.c_double), ("xi0", ctypes.c_double),
+                ("Zd", ctypes.c_double)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libtc_gb300.so is not built (run __graft_entry__.build()); no CPU fallback exists")
@@ -102,6 +143,11 @@ def _load():
     L.tc_mlp_train_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]
     L.tc_mlp_blob_bytes.restype = ctypes.c_size_t
+    L.tc_sixray.argtypes = [ctypes.POINTER(tc_sixray_grid)] + [ctypes.c_void_p] * 8
+    L.tc_pdr_spec_default.argtypes = [ctypes.POINTER(tc_pdr_spec)]
+    L.tc_pdr.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_pdr_spec), ctypes.POINTER(tc_pdr_out), ctypes.c_void_p]
+    L.tc_eq_spec_default.argtypes = [ctypes.POINTER(tc_eq_spec)]
+    L.tc_eq_curves.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_eq_spec), ctypes.POINTER(tc_eq_out), ctypes.c_void_p]
     L.tc_mlp_export.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
     return L
 
@@ -291,6 +337,12 @@ class Stepper:
     def load_mlp(self, blob: bytes) -> None:
         tc_load_mlp(self.h, blob)
 
+    def eq_curves(self, n_axis, chi0, xi0, Zg, Zd, shielded: bool = False, stream=None, **spec) -> dict:
+        return tc_eq_curves(self.h, n_axis, chi0, xi0, Zg, Zd, shielded, stream, **spec)
+
+    def pdr(self, n, chi0, xi0, Z, dx_cm, ncell: int, stream=None, **spec) -> dict:
+        return tc_pdr(self.h, n, chi0, xi0, Z, dx_cm, ncell, stream, **spec)
+
     def launches(self) -> int:
         return tc_launch_count(self.h)
 
@@ -304,6 +356,91 @@ class Stepper:
             self.close()
         except Exception:
             pass
+
+
+def _f64_host(v):
+    import numpy as np
+    return np.ascontiguousarray(np.atleast_1d(np.asarray(v, dtype=np.float64)))
+
+
+def tc_eq_curves(h, n_axis, chi0, xi0, Zg, Zd, shielded: bool = False, stream=None, out: dict | None = None,
+                 **spec) -> dict:
+    """Runs tc_eq_curves for the density axis `n_axis` and per-curve chi0, xi0, Zg, Zd
+    (host arrays); `spec` overrides tc_eq_spec fields (t_end_s, nchunk, L_shld0_pc, ...).
+    Returns device tensors of shape [ncurve, nn] (T, xH2, xHp, xe, P, xCO, chg, status)
+    and [ncurve] (i_max, i_min); `out` may pass preallocated ones."""
+    import torch
+    n_axis = _f64_host(n_axis)
+    cur = [_f64_host(v) for v in (chi0, xi0, Zg, Zd)]
+    nc = cur[0].size
+    if any(c.size != nc for c in cur):
+        raise ValueError("chi0, xi0, Zg, Zd must have the same length")
+    s = tc_eq_spec()
+    _check(lib.tc_eq_spec_default(ctypes.byref(s)), "tc_eq_spec_default")
+    s.n_axis, s.nn = n_axis.ctypes.data, n_axis.size
+    s.chi0, s.xi0, s.Zg, s.Zd = (c.ctypes.data for c in cur)
+    s.ncurve, s.shielded = nc, int(bool(shielded))
+    for k, v in spec.items():
+        setattr(s, k, v)
+    if out is None:
+        shape = (nc, n_axis.size)
+        out = {k: torch.empty(shape, dtype=torch.float64, device="cuda")
+               for k in ("T", "xH2", "xHp", "xe", "P", "xCO", "chg")}
+        out["status"] = torch.empty(shape, dtype=torch.int32, device="cuda")
+        out["i_max"] = torch.empty(nc, dtype=torch.int32, device="cuda")
+        out["i_min"] = torch.empty(nc, dtype=torch.int32, device="cuda")
+    o = tc_eq_out(*[out[k].data_ptr() if out.get(k) is not None else None
+                    for k in ("T", "xH2", "xHp", "xe", "P", "xCO", "chg", "status", "i_max", "i_min")])
+    _check(lib.tc_eq_curves(h, ctypes.byref(s), ctypes.byref(o), _stream_ptr(stream)), "tc_eq_curves")
+    return out
+
+
+def tc_pdr(h, n, chi0, xi0, Z, dx_cm, ncell: int, stream=None, out: dict | None = None, **spec) -> dict:
+    """Runs tc_pdr for slabs with per-slab n, chi0, xi0, Z (= Z'_g = Z'_d) and dx_cm (host
+    arrays); `spec` overrides tc_pdr_spec fields.  Returns device tensors [nslab, ncell]
+    (T, xH2, xHp, xe, xCO, chi_pe, f_h2, N_c, status) and [nslab] (N_trans)."""
+    import torch
+    arrs = [_f64_host(v) for v in (n, chi0, xi0, Z, dx_cm)]
+    ns = arrs[0].size
+    if any(a.size != ns for a in arrs):
+        raise ValueError("n, chi0, xi0, Z and dx_cm must have the same length")
+    s = tc_pdr_spec()
+    _check(lib.tc_pdr_spec_default(ctypes.byref(s)), "tc_pdr_spec_default")
+    s.n, s.chi0, s.xi0, s.Z, s.dx_cm = (a.ctypes.data for a in arrs)
+    s.nslab, s.ncell = ns, int(ncell)
+    for k, v in spec.items():
+        setattr(s, k, v)
+    if out is None:
+        shape = (ns, max(int(ncell), 0))
+        out = {k: torch.empty(shape, dtype=torch.float64, device="cuda")
+               for k in ("T", "xH2", "xHp", "xe", "xCO", "chi_pe", "f_h2", "N_c")}
+        out["status"] = torch.empty(shape, dtype=torch.int32, device="cuda")
+        out["N_trans"] = torch.empty(ns, dtype=torch.float64, device="cuda")
+    o = tc_pdr_out(*[out[k].data_ptr() if out.get(k) is not None else None
+                     for k in ("T", "xH2", "xHp", "xe", "xCO", "chi_pe", "f_h2", "N_c", "status", "N_trans")])
+    _check(lib.tc_pdr(h, ctypes.byref(s), ctypes.byref(o), _stream_ptr(stream)), "tc_pdr")
+    return out
+
+
+def tc_sixray(n, x_h2, dx_cm: float, chi0: float = 1.0, xi0: float = 2e-16, Zd: float = 1.0, out: dict | None = None,
+              n_eff: bool = True, stream=None) -> dict:
+    """Six-ray fields of a grid: n and x_h2 are device float64 tensors of shape
+    [nz, ny, nx].  Returns (or fills `out`) chi_pe, chi_lw, f_h2, xi and, if n_eff, N_eff."""
+    import torch
+    if n.dim() != 3 or n.shape != x_h2.shape or n.dtype != torch.float64 or x_h2.dtype != torch.float64:
+        raise ValueError("n and x_h2 must be float64 tensors of the same 3-d shape")
+    if not (n.is_contiguous() and x_h2.is_contiguous()):
+        raise ValueError("n and x_h2 must be contiguous")
+    nz, ny, nx = n.shape
+    g = tc_sixray_grid(nx, ny, nz, float(dx_cm), float(chi0), float(xi0), float(Zd))
+    if out is None:
+        keys = ("chi_pe", "chi_lw", "f_h2", "xi") + (("N_eff",) if n_eff else ())
+        out = {k: torch.empty_like(n) for k in keys}
+    ne = out.get("N_eff")
+    _check(lib.tc_sixray(ctypes.byref(g), n.data_ptr(), x_h2.data_ptr(), out["chi_pe"].data_ptr(),
+                         out["chi_lw"].data_ptr(), out["f_h2"].data_ptr(), out["xi"].data_ptr(),
+                         ne.data_ptr() if ne is not None else None, _stream_ptr(stream)), "tc_sixray")
+    return out
 
 
 def step_numpy(cells: dict, dt: float, mode: int = TC_MODE_PAPER_FP64, **params) -> dict:
