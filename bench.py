@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-peaks", action="store_true", help="skip the pipe microbenchmarks (no roofline)")
+    ap.add_argument("--no-drivers", action="store_true",
+                    help="skip the one-zone, six-ray and PDR legs (timed after the step)")
     return ap.parse_args()
 
 
@@ -248,12 +250,166 @@ def run_gpu(args):
 
     head = modes[0]
     e2e = None if args.no_e2e else run_e2e(args, tc, torch, cells, ncell, mode_ids[head], stream, barrier, ws)
+    drivers = None
+    if rank == 0 and not args.no_drivers:
+        drivers = {"onezone": run_onezone(args, tc, torch, stream), "sixray": run_sixray(args, tc, torch, stream, peaks),
+                   "pdr": run_pdr(args, tc, torch, stream)}
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     if rank != 0:
         return None
-    return report(args, results, head, ncell, peaks, e2e, clocks, cells, ws)
+    out = report(args, results, head, ncell, peaks, e2e, clocks, cells, ws)
+    out["drivers"] = drivers
+    return out
+
+
+def _time_call(fn, stream, reps, flush=None):
+    """Median CUDA-event time (ms) of fn() on `stream` over `reps` calls after one
+    warm-up; `flush` (a large tensor) is overwritten before each timed call."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return float(np.median(times))
+
+
+# One-zone equilibrium curves (Sec. 7.1, Fig. f:minmax): 64 FUV intensities chi0 in
+# [0.1, 1e3] (xi0 = 2e-16 chi0) x 4 metallicities Z' = Z'_g = Z'_d in {0.1, 0.3, 1, 3},
+# 512 densities in [1e-2, 1e4] cm^-3, 1e2 Myr in 10 chunks, FP64 Newton, k_gr = 3e-17 Z'_d.
+ONEZONE = dict(nchi=64, Z=(0.1, 0.3, 1.0, 3.0), nn=512, lo=-2.0, hi=4.0, t_end_myr=100.0, nchunk=10)
+
+
+def onezone_grid():
+    o = ONEZONE
+    chi = np.logspace(-1, 3, o["nchi"])
+    chi0 = np.repeat(chi, len(o["Z"]))
+    Z = np.tile(np.array(o["Z"]), o["nchi"])
+    return np.logspace(o["lo"], o["hi"], o["nn"]), chi0, 2e-16 * chi0, Z, Z
+
+
+def run_onezone(args, tc, torch, stream):
+    """Times tc_eq_curves on the Fig. f:minmax grid; the oracle's driver is timed on a
+    seeded sample of 16 of its curves."""
+    n_axis, chi0, xi0, Zg, Zd = onezone_grid()
+    t_end = ONEZONE["t_end_myr"] * 1e6 * 3.15576e7
+    st = tc.Stepper(tc.TC_MODE_NEWTON_FP64, flags=tc.TC_CONST_KGR)
+    kw = dict(t_end_s=t_end, nchunk=ONEZONE["nchunk"])
+    out = st.eq_curves(n_axis, chi0, xi0, Zg, Zd, stream=stream, **kw)
+    l0 = st.launches()
+    reps = max(1, min(args.steps, 3))
+    ms = _time_call(lambda: st.eq_curves(n_axis, chi0, xi0, Zg, Zd, stream=stream, out=out, **kw), stream, reps)
+    launches = (st.launches() - l0) // (reps + 1)
+    st.close()
+    ncell = n_axis.size * chi0.size
+    res = {"workload": "%d curves (64 chi0 in [0.1, 1e3] x Z' in %s) x %d densities in [1e-2, 1e4] cm^-3, "
+                       "1e2 Myr in %d chunks, FP64 Newton" % (chi0.size, list(ONEZONE["Z"]), n_axis.size,
+                                                             ONEZONE["nchunk"]),
+           "cells": ncell, "ms": ms, "cell_equilibria_per_s": ncell / (ms * 1e-3),
+           "curves_per_s": chi0.size / (ms * 1e-3), "gpu_launches": launches,
+           "cells_not_ok": int(((out["status"] & tc.TC_ST_ERROR_MASK) != 0).sum().item()),
+           "curves_with_two_phases": int((out["i_min"] > 0).sum().item())}
+    if not args.no_cpu_baseline:
+        import oracle
+        from oracle import onezone as oz
+        pick = np.sort(np.random.default_rng(5).choice(chi0.size, 16, replace=False))
+        a = time.perf_counter()
+        oz.curves(n_axis, chi0[pick], xi0[pick], Zg[pick], Zd[pick],
+                  oracle.default_params(mode=1, flags=oracle.F_CONST_KGR), t_end=t_end, nchunk=ONEZONE["nchunk"])
+        el = time.perf_counter() - a
+        res["cpu_baseline"] = {"value": pick.size * n_axis.size / el, "unit": "cell-equilibria/s",
+                               "cores": os.cpu_count() or 1, "kind": "oracle",
+                               "sample": "%d seeded curves of the grid (%d cells), %.1f s" %
+                                         (pick.size, pick.size * n_axis.size, el)}
+    return res
+
+
+# FP64 operations per cell of tc_sixray, counted from the kernel source: per ray the
+# H2 self-shielding factor (3 divides, a square root, an exponential), the ray weight
+# (an exponential and a square root) and ~15 adds/multiplies with the scans; per cell
+# the two cell averages (expm1 and a divide each), the two fields (an exponential each),
+# f_shld,H2 and N_eff (a divide each, a logarithm) and the CR rate (a divide).
+SIXRAY_OPS = {"add": 50.0, "mul": 40.0, "div": 23.0, "sqrt": 12.0, "exp": 16.0, "log": 1.0}
+
+
+def run_sixray(args, tc, torch, stream, peaks):
+    """Times tc_sixray on the slab's densities and H2 fractions laid out on 128^3 and
+    256^3 grids of 4 pc cells (L2 flushed before each call); the oracle is timed on the
+    64^3 corner of the first."""
+    res = {}
+    dx = 4.0 * 3.0856775814913673e18
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    for side in (128, 256):
+        c = synthgen.slab(side=side, key=2)
+        n = torch.from_numpy(np.ascontiguousarray(c["n"].reshape(side, side, side))).cuda()
+        x = torch.from_numpy(np.ascontiguousarray(
+            np.broadcast_to(c["xH2"], c["n"].shape).reshape(side, side, side))).cuda()
+        out = tc.tc_sixray(n, x, dx, stream=stream)
+        ms = _time_call(lambda: tc.tc_sixray(n, x, dx, out=out, stream=stream), stream, max(3, args.steps), flush)
+        ncell = side ** 3
+        r = {"grid": "%d^3" % side, "cells": ncell, "ms": ms, "cells_per_s": ncell / (ms * 1e-3),
+             "gpu_launches": 3, "l2": "flushed before each call"}
+        if peaks is not None:
+            fl = flops_per_cell(SIXRAY_OPS, peaks["weights"])
+            ach = fl * ncell / (ms * 1e-3) / 1e12
+            pk = 2.0 * peaks["fp64_fma_per_s"] / 1e12
+            r["roofline"] = {"bound": "alu", "pipe": "fp64", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                             "frac": ach / pk, "work": "FP64 ops per cell counted from the kernels (%.0f flops)" % fl}
+        res["%d" % side] = r
+        del n, x, out
+    del flush
+    if not args.no_cpu_baseline:
+        from oracle import sixray as osr
+        c = synthgen.slab(side=128, key=2)
+        n = c["n"].reshape(128, 128, 128)[:64, :64, :64].copy()
+        x = np.broadcast_to(c["xH2"], c["n"].shape).reshape(128, 128, 128)[:64, :64, :64].copy()
+        a = time.perf_counter()
+        osr.sixray(n, x, dx)
+        el = time.perf_counter() - a
+        res["cpu_baseline"] = {"value": 64 ** 3 / el, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                               "sample": "64^3 corner of the 128^3 grid, numpy, %.2f s" % el}
+    return res
+
+
+def run_pdr(args, tc, torch, stream):
+    """Times tc_pdr on the Sec. 7.3 suite without CRs: 24 slabs (n = 10..1e4 x chi0 =
+    0.1..1e4), 400 cells each resolving the transition column by ~25 cells, 3e2 Myr in
+    300 chunks; the oracle is timed on one of its slabs."""
+    from oracle import pdr as opdr
+    nn, cc = np.meshgrid([10.0, 1e2, 1e3, 1e4], [0.1, 1.0, 10.0, 1e2, 1e3, 1e4])
+    n, chi0 = nn.ravel(), cc.ravel()
+    Nt = opdr.bialy_sternberg_ntrans(chi0, n)
+    dx = Nt / 25.0 / n
+    z = np.zeros_like(n)
+    one = np.ones_like(n)
+    t_end = 3e2 * 1e6 * 3.15576e7
+    st = tc.Stepper(tc.TC_MODE_NEWTON_FP64, flags=tc.TC_CONST_KGR)
+    out = st.pdr(n, chi0, z, one, dx, 400, stream=stream, t_end_s=t_end, nchunk=300)
+    ms = _time_call(lambda: st.pdr(n, chi0, z, one, dx, 400, stream=stream, out=out, t_end_s=t_end, nchunk=300),
+                    stream, 1)
+    st.close()
+    ratio = (out["N_trans"].cpu().numpy() / Nt)
+    res = {"workload": "24 slabs x 400 cells, 3e2 Myr in 300 chunks, FP64 Newton, no CRs", "ms": ms,
+           "slabs_per_s": n.size / (ms * 1e-3), "cell_chunks_per_s": n.size * 400 * 300 / (ms * 1e-3),
+           "N_trans_over_analytic": {"min": float(ratio.min()), "max": float(ratio.max())}}
+    if not args.no_cpu_baseline:
+        import oracle
+        a = time.perf_counter()
+        opdr.slabs(n[:1], chi0[:1], z[:1], one[:1], dx[:1], 400,
+                   oracle.default_params(mode=1, flags=oracle.F_CONST_KGR), t_end=t_end, nchunk=300)
+        el = time.perf_counter() - a
+        res["cpu_baseline"] = {"value": 1.0 / el, "unit": "slabs/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+                               "sample": "1 slab of the suite, %.1f s" % el}
+    return res
 
 
 def run_e2e(args, tc, torch, cells, ncell, mode_id, stream, barrier, ws):
