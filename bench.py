@@ -334,11 +334,11 @@ def run_onezone(args, tc, torch, stream):
 
 
 # FP64 operations per cell of tc_sixray, counted from the kernel source: per ray the
-# H2 self-shielding factor (3 divides, a square root, an exponential), the ray weight
+# H2 self-shielding factor (4 divides, a square root, an exponential), the ray weight
 # (an exponential and a square root) and ~15 adds/multiplies with the scans; per cell
 # the two cell averages (expm1 and a divide each), the two fields (an exponential each),
-# f_shld,H2 and N_eff (a divide each, a logarithm) and the CR rate (a divide).
-SIXRAY_OPS = {"add": 50.0, "mul": 40.0, "div": 23.0, "sqrt": 12.0, "exp": 16.0, "log": 1.0}
+# f_shld,H2 and N_eff (a divide each, a logarithm), the CR rate and the two chi0/6 (a divide each).
+SIXRAY_OPS = {"add": 50.0, "mul": 40.0, "div": 31.0, "sqrt": 12.0, "exp": 16.0, "log": 1.0}
 
 
 def run_sixray(args, tc, torch, stream, peaks):
