@@ -381,30 +381,33 @@ def run_sixray(args, tc, torch, stream, peaks):
 
 
 def run_pdr(args, tc, torch, stream):
-    """Times tc_pdr on the Sec. 7.3 suite without CRs: 24 slabs (n = 10..1e4 x chi0 =
-    0.1..1e4), 400 cells each resolving the transition column by ~25 cells, 3e2 Myr in
-    300 chunks; the oracle is timed on one of its slabs."""
+    """Times tc_pdr on the Sec. 7.3 suite without CRs: the 19 slabs of n = 10..1e4 x
+    chi0 = 0.1..1e4 whose transition column the paper could resolve (more than three
+    cells of >= 1e-3 pc), 100 cells each (N_trans over ~25 cells), 3e2 Myr in 300
+    chunks; the oracle is timed on one of its slabs."""
     from oracle import pdr as opdr
     nn, cc = np.meshgrid([10.0, 1e2, 1e3, 1e4], [0.1, 1.0, 10.0, 1e2, 1e3, 1e4])
     n, chi0 = nn.ravel(), cc.ravel()
     Nt = opdr.bialy_sternberg_ntrans(chi0, n)
+    keep = Nt / n >= 3 * 1e-3 * 3.0856775814913673e18
+    n, chi0, Nt = n[keep], chi0[keep], Nt[keep]
     dx = Nt / 25.0 / n
     z = np.zeros_like(n)
     one = np.ones_like(n)
     t_end = 3e2 * 1e6 * 3.15576e7
     st = tc.Stepper(tc.TC_MODE_NEWTON_FP64, flags=tc.TC_CONST_KGR)
-    out = st.pdr(n, chi0, z, one, dx, 400, stream=stream, t_end_s=t_end, nchunk=300)
-    ms = _time_call(lambda: st.pdr(n, chi0, z, one, dx, 400, stream=stream, out=out, t_end_s=t_end, nchunk=300),
+    out = st.pdr(n, chi0, z, one, dx, 100, stream=stream, t_end_s=t_end, nchunk=300)
+    ms = _time_call(lambda: st.pdr(n, chi0, z, one, dx, 100, stream=stream, out=out, t_end_s=t_end, nchunk=300),
                     stream, 1)
     st.close()
     ratio = (out["N_trans"].cpu().numpy() / Nt)
-    res = {"workload": "24 slabs x 400 cells, 3e2 Myr in 300 chunks, FP64 Newton, no CRs", "ms": ms,
-           "slabs_per_s": n.size / (ms * 1e-3), "cell_chunks_per_s": n.size * 400 * 300 / (ms * 1e-3),
+    res = {"workload": "%d slabs x 100 cells, 3e2 Myr in 300 chunks, FP64 Newton, no CRs" % n.size, "ms": ms,
+           "slabs_per_s": n.size / (ms * 1e-3), "cell_chunks_per_s": n.size * 100 * 300 / (ms * 1e-3),
            "N_trans_over_analytic": {"min": float(ratio.min()), "max": float(ratio.max())}}
     if not args.no_cpu_baseline:
         import oracle
         a = time.perf_counter()
-        opdr.slabs(n[:1], chi0[:1], z[:1], one[:1], dx[:1], 400,
+        opdr.slabs(n[:1], chi0[:1], z[:1], one[:1], dx[:1], 100,
                    oracle.default_params(mode=1, flags=oracle.F_CONST_KGR), t_end=t_end, nchunk=300)
         el = time.perf_counter() - a
         res["cpu_baseline"] = {"value": 1.0 / el, "unit": "slabs/s", "cores": os.cpu_count() or 1, "kind": "oracle",

@@ -54,11 +54,12 @@ def test_ragged_and_degenerate_shapes(tc, shape):
 
 
 def test_deep_columns_underflow(tc):
-    # columns up to ~1e25 cm^-2 (tau ~ 1e4): exp(-tau) underflows, the relative sums do not
-    n, x = _grid((16, 16, 300), key=5, mu=6.0, sig=0.5)
-    g = _gpu(tc, n, x, 2.0 * PC)
-    r = sr.sixray(n, x, 2.0 * PC)
-    assert np.all(r["chi_pe"][:, :, 150] == 0.0)
+    # ~3000 cm^-3 in 10 pc cells: tau ~ 90 per cell, ~1800 to the centre of a 40^3 cube,
+    # so exp(-tau) underflows in the interior while the relative ray sums do not
+    n, x = _grid((40, 40, 40), key=5, mu=8.0, sig=0.3)
+    g = _gpu(tc, n, x, 10.0 * PC)
+    r = sr.sixray(n, x, 10.0 * PC)
+    assert np.all(r["chi_pe"][15:25, 15:25, 15:25] == 0.0)
     for k in ("f_h2", "N_eff", "xi"):
         np.testing.assert_allclose(g[k], r[k], rtol=RTOL, atol=0, err_msg=k)
     for k in ("chi_pe", "chi_lw"):
