@@ -53,8 +53,8 @@ def beamed_fields(n, xH2, dx, chi0, xi0, Zd):
     n = np.asarray(n, dtype=np.float64)
     q = n * dx
     qh = (xH2 * n) * dx
-    N_in = np.cumsum(q) - q                # column in front of the cell
-    H_in = np.cumsum(qh) - qh
+    N_in = np.concatenate(([0.0], np.cumsum(q)[:-1]))     # column in front of the cell
+    H_in = np.concatenate(([0.0], np.cumsum(qh)[:-1]))
     sp, sl = SIGMA_PE * Zd, SIGMA_LW * Zd
     chi_pe = chi0 * np.exp(-sp * N_in) * cell_average(sp * q)
     chi_lw = chi0 * np.exp(-sl * N_in) * cell_average(sl * q)

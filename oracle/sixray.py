@@ -49,16 +49,29 @@ def cell_average(t):
     return np.where(t < 1e-8, 1.0 - 0.5 * t, -np.expm1(-safe) / safe)
 
 
+def exclusive_cumsum(a, axis):
+    """Sum of the elements before each one along `axis`, accumulated from the start."""
+    c = np.cumsum(a, axis=axis)
+    out = np.zeros_like(a)
+    dst = [slice(None)] * a.ndim
+    src = [slice(None)] * a.ndim
+    dst[axis] = slice(1, None)
+    src[axis] = slice(None, -1)
+    out[tuple(dst)] = c[tuple(src)]
+    return out
+
+
 def ray_columns(q, dx):
-    """Columns of q*dx from each of the six faces to each cell's near face: a list of
-    six arrays (rays along +x, -x, +y, -y, +z, -z), arrays indexed [z, y, x]."""
+    """Columns of q*dx from each of the six faces to each cell's near face, each
+    accumulated from its ray's entry face (Sec. 5.2: optical depths are integrated from
+    the domain boundary): a list of six arrays (rays along +x, -x, +y, -y, +z, -z),
+    arrays indexed [z, y, x]."""
     out = []
+    qd = q * dx
     for axis in (2, 1, 0):
-        c = np.cumsum(q * dx, axis=axis)
-        fwd = c - q * dx                                   # cells before this one
-        tot = np.take(c, [-1], axis=axis)
-        bwd = tot - c                                      # cells after this one
-        out += [fwd, np.maximum(bwd, 0.0)]
+        fwd = exclusive_cumsum(qd, axis)
+        bwd = np.flip(exclusive_cumsum(np.flip(qd, axis), axis), axis)
+        out += [fwd, bwd]
     return out
 
 
