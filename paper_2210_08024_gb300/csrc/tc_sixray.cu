@@ -7,13 +7,17 @@
 //   acc.Spe  (in chi_pe)     sum of exp(-sigma_PE (N_ray - Nmin))
 //   acc.Slw  (in chi_lw)     sum of exp(-sigma_LW (N_ray - Nmin))
 //   acc.Sh2  (in f_shld_h2)  sum of exp(-sigma_LW (N_ray - Nmin)) f_shld,H2(N_H2,ray)
-// A ray's column needs the sum of n dx over the cells before the cell and, for the
-// opposite ray, over the cells after it (the line total minus the inclusive prefix).
+// A ray's column is the sum of n dx over the cells between its entry face and the cell,
+// accumulated from that face (exclusive scans in both directions; a line total minus a
+// prefix would cancel to rounding noise near the far face, which the H2 self-shielding
+// factor resolves in its Doppler-core regime).
 //  * z and y passes: lines run across rows, so 32 neighbouring lines (consecutive x)
 //    form a warp and loads stay coalesced; each line is cut into 8 segments scanned by
 //    8 warps of a block, which combine their segment sums in shared memory (a two-level
-//    scan), so even a 128^3 grid gives 131k threads.
-//  * x pass: a line is a contiguous row; one warp scans it in chunks of 32 with shuffles.
+//    scan), so even a 128^3 grid gives 131k threads.  Each segment is swept forwards
+//    (the ray entering at the low face) and backwards (the ray entering at the high face).
+//  * x pass: a line is a contiguous row; one warp scans it in chunks of 32 with shuffles,
+//    backwards first, then forwards, where it also converts the accumulators.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -105,34 +109,44 @@ __global__ void __launch_bounds__(32 * SEG) k_sr_lines(long long nx, long long l
   sN[seg][lane] = sn;
   sH[seg][lane] = sh;
   __syncthreads();
-  double offN = 0.0, offH = 0.0, totN = 0.0, totH = 0.0;
-  for (int s = 0; s < SEG; ++s) {
-    if (s == seg) { offN = totN; offH = totH; }
-    totN += sN[s][lane];
-    totH += sH[s][lane];
-  }
+  // columns of the segments before this one (from the low face) and after it (from the
+  // high face)
+  double fN = 0.0, fH = 0.0, bN = 0.0, bH = 0.0;
+  for (int s = 0; s < seg; ++s) { fN += sN[s][lane]; fH += sH[s][lane]; }
+  for (int s = SEG - 1; s > seg; --s) { bN += sN[s][lane]; bH += sH[s][lane]; }
   if (!live) return;
-  double runN = offN, runH = offH;
   for (long long c = c0; c < c1; ++c) {
     const long long e = base + c * lstride;
     const double nn = n[e];
     const double ownN = nn * k.dx;
     const double ownH = (xh2[e] * nn) * k.dx;
     const double half = 0.5 * xh2[e] * nn * k.dx;
-    const double inN = runN + ownN, inH = runH + ownH;
     Acc a;
     if (FIRST) a = Acc{0.0, 0.0, 0.0, 0.0};
     else a = load_acc(chi_pe, chi_lw, fh2, xi, e);
-    add_ray(a, k, runN, runH + half);
-    add_ray(a, k, fmax(totN - inN, 0.0), fmax(totH - inH, 0.0) + half);
+    add_ray(a, k, fN, fH + half);
     store_acc(chi_pe, chi_lw, fh2, xi, e, a);
-    runN = inN;
-    runH = inH;
+    fN += ownN;
+    fH += ownH;
+  }
+  for (long long c = c1 - 1; c >= c0; --c) {
+    const long long e = base + c * lstride;
+    const double nn = n[e];
+    const double ownN = nn * k.dx;
+    const double ownH = (xh2[e] * nn) * k.dx;
+    const double half = 0.5 * xh2[e] * nn * k.dx;
+    Acc a = load_acc(chi_pe, chi_lw, fh2, xi, e);
+    add_ray(a, k, bN, bH + half);
+    store_acc(chi_pe, chi_lw, fh2, xi, e, a);
+    bN += ownN;
+    bH += ownH;
   }
 }
 
-// Rows along x: one warp per row, chunks of 32 cells scanned with shuffles; adds the
-// two x rays and converts the accumulators into the fields.
+// Rows along x: one warp per row, chunks of 32 cells scanned with shuffles: the ray
+// entering at the high face first (suffix scans, last chunk first), then the ray
+// entering at the low face (prefix scans), which also converts the accumulators into
+// the fields.
 __global__ void __launch_bounds__(256) k_sr_rows(long long nx, long long nrows, SrConst k,
                                                  const double* __restrict__ n, const double* __restrict__ xh2,
                                                  double* chi_pe, double* chi_lw, double* fh2, double* xi,
@@ -141,23 +155,40 @@ __global__ void __launch_bounds__(256) k_sr_rows(long long nx, long long nrows, 
   const int lane = threadIdx.x & 31;
   if (row >= nrows) return;
   const long long base = row * nx;
-  double tN = 0.0, tH = 0.0;
-  for (long long i = lane; i < nx; i += 32) {
-    tN += n[base + i] * k.dx;
-    tH += (xh2[base + i] * n[base + i]) * k.dx;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    tN += __shfl_xor_sync(0xffffffffu, tN, o);
-    tH += __shfl_xor_sync(0xffffffffu, tH, o);
-  }
+  const long long nchunk = (nx + 31) / 32;
   double carryN = 0.0, carryH = 0.0;
+  for (long long ch = nchunk - 1; ch >= 0; --ch) {
+    const long long i = ch * 32 + lane;
+    const bool live = i < nx;
+    const double nn = live ? n[base + i] : 0.0;
+    const double xx = live ? xh2[base + i] : 0.0;
+    double iN = nn * k.dx, iH = (xx * nn) * k.dx;  // inclusive suffix scan within the chunk
+    for (int d = 1; d < 32; d <<= 1) {
+      const double vN = __shfl_down_sync(0xffffffffu, iN, d);
+      const double vH = __shfl_down_sync(0xffffffffu, iH, d);
+      if (lane + d < 32) { iN += vN; iH += vH; }
+    }
+    double eN = __shfl_down_sync(0xffffffffu, iN, 1), eH = __shfl_down_sync(0xffffffffu, iH, 1);
+    if (lane == 31) { eN = 0.0; eH = 0.0; }
+    const double chunkN = __shfl_sync(0xffffffffu, iN, 0), chunkH = __shfl_sync(0xffffffffu, iH, 0);
+    if (live) {
+      const long long e = base + i;
+      const double half = 0.5 * xx * nn * k.dx;
+      Acc a = load_acc(chi_pe, chi_lw, fh2, xi, e);
+      add_ray(a, k, carryN + eN, carryH + eH + half);
+      store_acc(chi_pe, chi_lw, fh2, xi, e, a);
+    }
+    carryN += chunkN;
+    carryH += chunkH;
+  }
+  carryN = 0.0;
+  carryH = 0.0;
   for (long long i0 = 0; i0 < nx; i0 += 32) {
     const long long i = i0 + lane;
     const bool live = i < nx;
     const double nn = live ? n[base + i] : 0.0;
     const double xx = live ? xh2[base + i] : 0.0;
-    const double ownN = nn * k.dx, ownH = (xx * nn) * k.dx;
-    double iN = ownN, iH = ownH;  // inclusive scan within the chunk
+    double iN = nn * k.dx, iH = (xx * nn) * k.dx;  // inclusive prefix scan within the chunk
     for (int d = 1; d < 32; d <<= 1) {
       const double vN = __shfl_up_sync(0xffffffffu, iN, d);
       const double vH = __shfl_up_sync(0xffffffffu, iH, d);
@@ -169,11 +200,8 @@ __global__ void __launch_bounds__(256) k_sr_rows(long long nx, long long nrows, 
     if (live) {
       const long long e = base + i;
       const double half = 0.5 * xx * nn * k.dx;
-      const double fwdN = carryN + eN, fwdH = carryH + eH;
-      const double inN = carryN + iN, inH = carryH + iH;
       Acc a = load_acc(chi_pe, chi_lw, fh2, xi, e);
-      add_ray(a, k, fwdN, fwdH + half);
-      add_ray(a, k, fmax(tN - inN, 0.0), fmax(tH - inH, 0.0) + half);
+      add_ray(a, k, carryN + eN, carryH + eH + half);
       // fields of the cell
       const double gpe = cell_average(k.spe * nn * k.dx);
       const double glw = cell_average(k.slw * nn * k.dx);
