@@ -351,8 +351,7 @@ def run_sixray(args, tc, torch, stream, peaks):
     for side in (128, 256):
         c = synthgen.slab(side=side, key=2)
         n = torch.from_numpy(np.ascontiguousarray(c["n"].reshape(side, side, side))).cuda()
-        x = torch.from_numpy(np.ascontiguousarray(
-            np.broadcast_to(c["xH2"], c["n"].shape).reshape(side, side, side))).cuda()
+        x = torch.from_numpy(np.array(np.broadcast_to(c["xH2"], c["n"].shape).reshape(side, side, side))).cuda()
         out = tc.tc_sixray(n, x, dx, stream=stream)
         ms = _time_call(lambda: tc.tc_sixray(n, x, dx, out=out, stream=stream), stream, max(3, args.steps), flush)
         ncell = side ** 3
@@ -380,38 +379,50 @@ def run_sixray(args, tc, torch, stream, peaks):
     return res
 
 
-def run_pdr(args, tc, torch, stream):
-    """Times tc_pdr on the Sec. 7.3 suite without CRs: the 19 slabs of n = 10..1e4 x
-    chi0 = 0.1..1e4 whose transition column the paper could resolve (more than three
-    cells of >= 1e-3 pc), 100 cells each (N_trans over ~25 cells), 3e2 Myr in 300
-    chunks; the oracle is timed on one of its slabs."""
+def pdr_suite():
+    """Sec. 7.3 suites, batched: n_H in 16 values over [10, 1e4] x chi0 in 16 values over
+    [0.1, 1e4] x xi0 in {0, 2e-18, 2e-17, 2e-16} s^-1, keeping the slabs whose transition
+    column the paper could resolve (more than three cells of >= 1e-3 pc); 100 cells per
+    slab resolving the no-CR transition column by ~25 cells."""
     from oracle import pdr as opdr
-    nn, cc = np.meshgrid([10.0, 1e2, 1e3, 1e4], [0.1, 1.0, 10.0, 1e2, 1e3, 1e4])
-    n, chi0 = nn.ravel(), cc.ravel()
+    n, chi0, xi0 = (a.ravel() for a in np.meshgrid(np.logspace(1, 4, 16), np.logspace(-1, 4, 16),
+                                                    [0.0, 2e-18, 2e-17, 2e-16], indexing="ij"))
     Nt = opdr.bialy_sternberg_ntrans(chi0, n)
     keep = Nt / n >= 3 * 1e-3 * 3.0856775814913673e18
-    n, chi0, Nt = n[keep], chi0[keep], Nt[keep]
-    dx = Nt / 25.0 / n
-    z = np.zeros_like(n)
+    n, chi0, xi0, Nt = n[keep], chi0[keep], xi0[keep], Nt[keep]
+    return n, chi0, xi0, Nt, Nt / 25.0 / n
+
+
+def run_pdr(args, tc, torch, stream):
+    """Times tc_pdr on the batched suites (3e2 Myr in 300 chunks, FP64 Newton); the
+    oracle is timed on 8 of the slabs."""
+    from oracle import pdr as opdr
+    n, chi0, xi0, Nt, dx = pdr_suite()
     one = np.ones_like(n)
     t_end = 3e2 * 1e6 * 3.15576e7
     st = tc.Stepper(tc.TC_MODE_NEWTON_FP64, flags=tc.TC_CONST_KGR)
-    out = st.pdr(n, chi0, z, one, dx, 100, stream=stream, t_end_s=t_end, nchunk=300)
-    ms = _time_call(lambda: st.pdr(n, chi0, z, one, dx, 100, stream=stream, out=out, t_end_s=t_end, nchunk=300),
+    out = st.pdr(n, chi0, xi0, one, dx, 100, stream=stream, t_end_s=t_end, nchunk=300)
+    l0 = st.launches()
+    ms = _time_call(lambda: st.pdr(n, chi0, xi0, one, dx, 100, stream=stream, out=out, t_end_s=t_end, nchunk=300),
                     stream, 1)
+    launches = (st.launches() - l0) // 2
     st.close()
-    ratio = (out["N_trans"].cpu().numpy() / Nt)
-    res = {"workload": "%d slabs x 100 cells, 3e2 Myr in 300 chunks, FP64 Newton, no CRs" % n.size, "ms": ms,
-           "slabs_per_s": n.size / (ms * 1e-3), "cell_chunks_per_s": n.size * 100 * 300 / (ms * 1e-3),
-           "N_trans_over_analytic": {"min": float(ratio.min()), "max": float(ratio.max())}}
+    nocr = xi0 == 0.0
+    ratio = out["N_trans"].cpu().numpy()[nocr] / Nt[nocr]
+    res = {"workload": "%d slabs x 100 cells (n 10..1e4, chi0 0.1..1e4, xi0 0..2e-16), 3e2 Myr in 300 chunks, "
+                       "FP64 Newton" % n.size, "ms": ms, "slabs_per_s": n.size / (ms * 1e-3),
+           "cell_chunks_per_s": n.size * 100 * 300 / (ms * 1e-3), "gpu_launches": launches,
+           "cells_not_ok": int(((out["status"] & tc.TC_ST_ERROR_MASK) != 0).sum().item()),
+           "N_trans_over_analytic_no_cr": {"min": float(ratio.min()), "max": float(ratio.max())}}
     if not args.no_cpu_baseline:
         import oracle
+        pick = np.sort(np.random.default_rng(6).choice(n.size, 8, replace=False))
         a = time.perf_counter()
-        opdr.slabs(n[:1], chi0[:1], z[:1], one[:1], dx[:1], 100,
+        opdr.slabs(n[pick], chi0[pick], xi0[pick], one[pick], dx[pick], 100,
                    oracle.default_params(mode=1, flags=oracle.F_CONST_KGR), t_end=t_end, nchunk=300)
         el = time.perf_counter() - a
-        res["cpu_baseline"] = {"value": 1.0 / el, "unit": "slabs/s", "cores": os.cpu_count() or 1, "kind": "oracle",
-                               "sample": "1 slab of the suite, %.1f s" % el}
+        res["cpu_baseline"] = {"value": pick.size / el, "unit": "slabs/s", "cores": os.cpu_count() or 1,
+                               "kind": "oracle", "sample": "8 seeded slabs of the suite, %.1f s" % el}
     return res
 
 
