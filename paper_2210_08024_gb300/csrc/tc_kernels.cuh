@@ -597,8 +597,16 @@ TCG_FN bool mlp_seed(const MlpDev* w, float* buf0, float* buf1, int st, const fl
 }
 
 // ------------------------------------------------------------------ the kernel
+// Registers: 128 threads per block and at least 4 resident blocks per SM (128 registers
+// per thread, some spilled to L1) measured faster than the 168 registers and 3 blocks
+// the compiler picks on its own: 510 vs 546 ms (FP64 Newton) and 352 vs 403 ms (mixed)
+// on the 128^3 slab.  The seeded modes keep 2 blocks: their shared-memory weights and
+// activations (~84 KB per block) allow no more.
+template <int MODE>
+constexpr int step_min_blocks() { return (MODE == 3 || MODE == 4) ? 2 : 4; }
+
 template <int MODE, bool BATCH>
-__global__ void __launch_bounds__(128) k_step(DevFields f1, const BoxTable* __restrict__ boxes, DevParams p,
+__global__ void __launch_bounds__(128, step_min_blocks<MODE>()) k_step(DevFields f1, const BoxTable* __restrict__ boxes, DevParams p,
                                                double dt, unsigned long long* cursor, long long ntotal,
                                                const MlpDev* __restrict__ mlp) {
   constexpr bool SEEDED = (MODE == 3 || MODE == 4);
