@@ -57,6 +57,11 @@ struct LaneState {
   double t, Tmu, xH2, xHp, mu;
   double xe, xCp, xCO, Td;
   int nsub, status, iters;
+  // mode 1, the substep in progress: its length, the Newton iterate, the iterations
+  // and halvings so far, and whether it ends the step
+  double dts, y[3];
+  int it, halv;
+  bool last, open;
 };
 
 TCG_FN void load_cell(const DevFields& f, long long i, const DevParams& p, CellC<double>& c,
@@ -256,51 +261,60 @@ TCG_FN bool damped_step(double* y, const double* d, double* st) {
   return full;
 }
 
-// One Newton solve of y - y^n - dts f(y) = 0 from `y` (seed on entry, root on exit),
-// forward-difference Jacobian every iteration (relative step 1e-7, abundance steps
-// floored at 1e-17), converged when every full step is below rtol |y_i|.
-// Returns iterations used, or -1.
+// One Newton iteration on y - y^n - dts f(y) = 0: forward-difference Jacobian
+// (relative step 1e-7, abundance steps floored at 1e-17), a damped step, and the test
+// that every full step is below rtol |y_i|.  Returns 1 when converged, 0 to continue,
+// -1 on failure (singular Jacobian or a non-finite state).
+TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
+                       double dts, double* y, double& xe_g, double& td_g) {
+  TCG_COUNT_D(newton64_it);
+  double f0[3], J[3][3];
+  ChemT<double> b = chem_T(c, mu * y[0], p.flags);
+  CoolT<double> k = cool_T(c, b, p.flags);
+  // evaluation order: x_H2 column, x_H+ column, base point (all at the base T), then
+  // the T_mu column, so the temperature blocks are built twice per iteration.
+  double fx[2][3];
+#pragma unroll 1
+  for (int j = 1; j < 3; ++j) {
+    double h = fmax(1e-7 * fabs(y[j]), 1e-17);
+    double y1 = y[1] + ((j == 1) ? h : 0.0), y2 = y[2] + ((j == 2) ? h : 0.0);
+    double xg = xe_g, tg = td_g;
+    feval64(c, b, k, y1, y2, Kinv, xg, tg, fx[j - 1]);
+  }
+  feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0);
+  for (int j = 1; j < 3; ++j) {
+    double h = fmax(1e-7 * fabs(y[j]), 1e-17);
+    for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - dts * (fx[j - 1][i] - f0[i]) / h;
+  }
+  {
+    double h = 1e-7 * y[0];
+    ChemT<double> bT = chem_T(c, mu * (y[0] + h), p.flags);
+    CoolT<double> kT = cool_T(c, bT, p.flags);
+    double xg = xe_g, tg = td_g;
+    double fT[3];
+    feval64(c, bT, kT, y[1], y[2], Kinv, xg, tg, fT);
+    for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - dts * (fT[i] - f0[i]) / h;
+  }
+  double rhs[3], d[3];
+  for (int i = 0; i < 3; ++i) rhs[i] = -(y[i] - yn[i] - dts * f0[i]);
+  if (!solve3(J, rhs, d)) return -1;
+  double st[3];
+  bool conv = damped_step(y, d, st);
+  for (int i = 0; i < 3; ++i)
+    if (fabs(st[i]) > p.rtol * fabs(y[i]) + 1e-300) conv = false;
+  if (!finite3(y[0], y[1], y[2])) return -1;
+  return conv ? 1 : 0;
+}
+
+// One Newton solve from `y` (seed on entry, root on exit).  Returns the iterations
+// used, or -1.
 TCG_FN int newton_solve(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
                         double dts, double* y, double& xe_g, double& td_g, int maxit = 0) {
   const int nmax = (maxit > 0 && maxit < p.newton_max) ? maxit : p.newton_max;
   for (int it = 1; it <= nmax; ++it) {
-    TCG_COUNT_D(newton64_it);
-    double f0[3], J[3][3];
-    ChemT<double> b = chem_T(c, mu * y[0], p.flags);
-    CoolT<double> k = cool_T(c, b, p.flags);
-    // evaluation order: x_H2 column, x_H+ column, base point (all at the base T), then
-    // the T_mu column, so the temperature blocks are built twice per iteration.
-    double fx[2][3];
-#pragma unroll 1
-    for (int j = 1; j < 3; ++j) {
-      double h = fmax(1e-7 * fabs(y[j]), 1e-17);
-      double y1 = y[1] + ((j == 1) ? h : 0.0), y2 = y[2] + ((j == 2) ? h : 0.0);
-      double xg = xe_g, tg = td_g;
-      feval64(c, b, k, y1, y2, Kinv, xg, tg, fx[j - 1]);
-    }
-    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0);
-    for (int j = 1; j < 3; ++j) {
-      double h = fmax(1e-7 * fabs(y[j]), 1e-17);
-      for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - dts * (fx[j - 1][i] - f0[i]) / h;
-    }
-    {
-      double h = 1e-7 * y[0];
-      ChemT<double> bT = chem_T(c, mu * (y[0] + h), p.flags);
-      CoolT<double> kT = cool_T(c, bT, p.flags);
-      double xg = xe_g, tg = td_g;
-      double fT[3];
-      feval64(c, bT, kT, y[1], y[2], Kinv, xg, tg, fT);
-      for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - dts * (fT[i] - f0[i]) / h;
-    }
-    double rhs[3], d[3];
-    for (int i = 0; i < 3; ++i) rhs[i] = -(y[i] - yn[i] - dts * f0[i]);
-    if (!solve3(J, rhs, d)) return -1;
-    double st[3];
-    bool conv = damped_step(y, d, st);
-    for (int i = 0; i < 3; ++i)
-      if (fabs(st[i]) > p.rtol * fabs(y[i]) + 1e-300) conv = false;
-    if (!finite3(y[0], y[1], y[2])) return -1;
-    if (conv) return it;
+    const int r = newton_iter(c, p, mu, Kinv, yn, dts, y, xe_g, td_g);
+    if (r < 0) return -1;
+    if (r > 0) return it;
   }
   return -1;
 }
@@ -396,6 +410,46 @@ TCG_FN void substep_newton64(const CellC<double>& c, const DevParams& p, double 
   bool last;
   const double dts = substep_start64(c, p, dt, s, td_g, last);
   solve_substep64(c, p, dt, dts, last, s, xe_g, td_g);
+}
+
+// One trip of the mode-1 lane loop: opens a substep if none is in progress (its length
+// from the start-state sources, Sec. 6.1), then takes exactly one Newton iteration; a
+// converged iterate closes the substep, a failed solve halves it (up to 30 times) and
+// restarts from the start state.  The same sequence of operations as solve_substep64,
+// cut at iteration boundaries: the lanes of a warp then run their Newton iterations
+// together whatever their substep, instead of waiting, substep by substep, for the
+// lane that needs the most iterations.
+TCG_FN void newton_trip(const CellC<double>& c, const DevParams& p, double dt, LaneState& s, double& xe_g,
+                        double& td_g) {
+  if (!s.open) {
+    s.dts = substep_start64(c, p, dt, s, td_g, s.last);
+    s.y[0] = s.Tmu; s.y[1] = s.xH2; s.y[2] = s.xHp;
+    s.it = 0;
+    s.halv = 0;
+    s.open = true;
+  }
+  const double yn[3] = {s.Tmu, s.xH2, s.xHp};
+  int r = newton_iter(c, p, s.mu, 1.0 / c.K, yn, s.dts, s.y, xe_g, td_g);
+  s.it += 1;
+  if (r == 0 && s.it >= p.newton_max) r = -1;
+  if (r < 0) {
+    if (s.halv < 30) {
+      s.status |= ST_NEWTON;
+      s.dts *= 0.5;
+      s.last = false;
+      s.halv += 1;
+      s.y[0] = yn[0]; s.y[1] = yn[1]; s.y[2] = yn[2];
+      s.it = 0;
+    } else {
+      s.status |= ST_NONFIN;
+      s.t = dt;
+      s.open = false;
+    }
+  } else if (r > 0) {
+    s.iters += s.it;
+    finish_substep<double>(c, c.muH, p, dt, s.dts, s.last, s.y, s);
+    s.open = false;
+  }
 }
 
 // ------------------------------------------------------------------ mode 2: mixed precision
@@ -660,6 +714,7 @@ __global__ void __launch_bounds__(128, step_min_blocks<MODE>()) k_step(DevFields
       s.nsub = 0;
       s.status = 0;
       s.iters = 0;
+      s.open = false;
       {
         // initial C/O/e equilibrium (it sets mu and hence T_mu) in FP64 for every mode
         ChemT<double> b0 = chem_T(c, T0, p.flags);
@@ -688,13 +743,13 @@ __global__ void __launch_bounds__(128, step_min_blocks<MODE>()) k_step(DevFields
       have = true;
     }
     if (s.t < dt) {
-      if (s.nsub >= p.max_sub) {
+      if (s.nsub >= p.max_sub && !(MODE == 1 && s.open)) {
         s.status |= ST_MAX_SUB;
         s.t = dt;
       } else if constexpr (MODE == 0) {
         substep_paper(c, p, dt, s);
       } else if constexpr (MODE == 1) {
-        substep_newton64(c, p, dt, s, xe_g, td_g);
+        newton_trip(c, p, dt, s, xe_g, td_g);
       } else if constexpr (MODE == 2) {
         substep_mixed(c, cf, p, dt, s, xe_gf, td_gf, td64);
       } else {
