@@ -57,11 +57,6 @@ struct LaneState {
   double t, Tmu, xH2, xHp, mu;
   double xe, xCp, xCO, Td;
   int nsub, status, iters;
-  // mode 1, the substep in progress: its length, the Newton iterate, the iterations
-  // and halvings so far, and whether it ends the step
-  double dts, y[3];
-  int it, halv;
-  bool last, open;
 };
 
 TCG_FN void load_cell(const DevFields& f, long long i, const DevParams& p, CellC<double>& c,
@@ -412,46 +407,6 @@ TCG_FN void substep_newton64(const CellC<double>& c, const DevParams& p, double 
   solve_substep64(c, p, dt, dts, last, s, xe_g, td_g);
 }
 
-// One trip of the mode-1 lane loop: opens a substep if none is in progress (its length
-// from the start-state sources, Sec. 6.1), then takes exactly one Newton iteration; a
-// converged iterate closes the substep, a failed solve halves it (up to 30 times) and
-// restarts from the start state.  The same sequence of operations as solve_substep64,
-// cut at iteration boundaries: the lanes of a warp then run their Newton iterations
-// together whatever their substep, instead of waiting, substep by substep, for the
-// lane that needs the most iterations.
-TCG_FN void newton_trip(const CellC<double>& c, const DevParams& p, double dt, LaneState& s, double& xe_g,
-                        double& td_g) {
-  if (!s.open) {
-    s.dts = substep_start64(c, p, dt, s, td_g, s.last);
-    s.y[0] = s.Tmu; s.y[1] = s.xH2; s.y[2] = s.xHp;
-    s.it = 0;
-    s.halv = 0;
-    s.open = true;
-  }
-  const double yn[3] = {s.Tmu, s.xH2, s.xHp};
-  int r = newton_iter(c, p, s.mu, 1.0 / c.K, yn, s.dts, s.y, xe_g, td_g);
-  s.it += 1;
-  if (r == 0 && s.it >= p.newton_max) r = -1;
-  if (r < 0) {
-    if (s.halv < 30) {
-      s.status |= ST_NEWTON;
-      s.dts *= 0.5;
-      s.last = false;
-      s.halv += 1;
-      s.y[0] = yn[0]; s.y[1] = yn[1]; s.y[2] = yn[2];
-      s.it = 0;
-    } else {
-      s.status |= ST_NONFIN;
-      s.t = dt;
-      s.open = false;
-    }
-  } else if (r > 0) {
-    s.iters += s.it;
-    finish_substep<double>(c, c.muH, p, dt, s.dts, s.last, s.y, s);
-    s.open = false;
-  }
-}
-
 // ------------------------------------------------------------------ mode 2: mixed precision
 // f(y) from FP32 source terms; the closure x_H and the net sums H = n G - n^2 L,
 // C_H2 = form - dest, C_H+ = ion - rec are formed in FP64 from the FP32 parts.
@@ -714,7 +669,6 @@ __global__ void __launch_bounds__(128, step_min_blocks<MODE>()) k_step(DevFields
       s.nsub = 0;
       s.status = 0;
       s.iters = 0;
-      s.open = false;
       {
         // initial C/O/e equilibrium (it sets mu and hence T_mu) in FP64 for every mode
         ChemT<double> b0 = chem_T(c, T0, p.flags);
@@ -743,13 +697,13 @@ __global__ void __launch_bounds__(128, step_min_blocks<MODE>()) k_step(DevFields
       have = true;
     }
     if (s.t < dt) {
-      if (s.nsub >= p.max_sub && !(MODE == 1 && s.open)) {
+      if (s.nsub >= p.max_sub) {
         s.status |= ST_MAX_SUB;
         s.t = dt;
       } else if constexpr (MODE == 0) {
         substep_paper(c, p, dt, s);
       } else if constexpr (MODE == 1) {
-        newton_trip(c, p, dt, s, xe_g, td_g);
+        substep_newton64(c, p, dt, s, xe_g, td_g);
       } else if constexpr (MODE == 2) {
         substep_mixed(c, cf, p, dt, s, xe_gf, td_gf, td64);
       } else {
