@@ -77,6 +77,13 @@ typedef struct tc_params {
   double newton_rtol_mixed;    /* step tolerance of the FP32 Newton iterations of the mixed modes; default 1e-7 */
   int block;                   /* threads per block (0 = autotuned/default) */
   int blocks_per_sm;           /* resident blocks per SM for the persistent grid (0 = occupancy) */
+  int order_cells;             /* 1 (default): hand cells to the persistent kernel in decreasing order of
+                                  their predicted substep count, dt over the first substep length of
+                                  Sec. 6.1 from the start-state sources (the library's scheduling, no
+                                  counterpart in the paper; results are the same in any order, the
+                                  longest cells then no longer finish last and warps hold cells of
+                                  similar cost); needs 5 bytes of device workspace per cell, grown by
+                                  cudaMalloc.  0: cells in index order. */
 } tc_params;
 
 typedef struct tc_fields {

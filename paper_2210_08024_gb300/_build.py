@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtc_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["tc_api.cu", "tc_onezone.cu", "tc_sixray.cu", "tc_pdr.cu", "tc_k_paper.cu", "tc_k_newton.cu", "tc_k_mixed.cu", "tc_mlp.cu", "tc_peak.cu",
+SOURCES = ["tc_api.cu", "tc_onezone.cu", "tc_sixray.cu", "tc_pdr.cu", "tc_order.cu", "tc_k_paper.cu", "tc_k_newton.cu", "tc_k_mixed.cu", "tc_mlp.cu", "tc_peak.cu",
            "tc_static.cu", "tc_k_seeded3.cu", "tc_k_seeded4.cu"]
 
 

@@ -16,6 +16,7 @@
 #include "../../include/tc_pdr.h"
 #include "tc_launch.h"
 #include "tc_onezone.cuh"
+#include "tc_order.cuh"
 #include "tc_pdr.cuh"
 
 namespace tcg {
@@ -46,6 +47,11 @@ struct tc_handle {
   // MLP seed weights (device) -- loaded by tc_load_mlp
   void* d_mlp = nullptr;
   size_t mlp_bytes = 0;
+  // cost-ordered work queue (tc_params.order_cells): class keys, histogram, order
+  unsigned char* d_okey = nullptr;
+  unsigned* d_ohist = nullptr;
+  unsigned* d_order = nullptr;
+  size_t order_cells = 0;
   // driver workspace (tc_eq_curves, tc_pdr): per-cell arrays and the parameter arrays
   double* d_eq = nullptr;
   int* d_eqi = nullptr;
@@ -87,6 +93,7 @@ int tc_params_default(tc_params* p, int mode) {
   p->newton_rtol_mixed = 1e-7;
   p->block = 0;
   p->blocks_per_sm = 0;
+  p->order_cells = 1;
   return TC_OK;
 }
 
@@ -126,6 +133,9 @@ void tc_destroy(tc_handle* h) {
   cudaFree(h->d_eq);
   cudaFree(h->d_eqi);
   cudaFree(h->d_eqpar);
+  cudaFree(h->d_okey);
+  cudaFree(h->d_ohist);
+  cudaFree(h->d_order);
   delete h;
 }
 
@@ -206,6 +216,33 @@ static void launch_shape(tc_handle* h, int kmode, long long ntotal, int* grid, i
   *block = b;
 }
 
+// Grows the cost-ordering workspace to ncell cells (not while `st` is being captured).
+// Returns false if there is none to use.
+static bool order_workspace(tc_handle* h, long long ncell, cudaStream_t st) {
+  if (ncell > 4000000000LL) return false;
+  if (h->order_cells >= (size_t)ncell && h->d_order) return true;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+  if (h->gexec) {  // the cached batched graph points at the old workspace
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  cudaFree(h->d_okey);
+  cudaFree(h->d_order);
+  h->d_okey = nullptr;
+  h->d_order = nullptr;
+  h->order_cells = 0;
+  if (!h->d_ohist && cudaMalloc(&h->d_ohist, tcg::ORDER_BUCKETS * sizeof(unsigned)) != cudaSuccess) return false;
+  if (cudaMalloc(&h->d_okey, (size_t)ncell) != cudaSuccess) return false;
+  if (cudaMalloc(&h->d_order, (size_t)ncell * sizeof(unsigned)) != cudaSuccess) {
+    cudaFree(h->d_okey);
+    h->d_okey = nullptr;
+    return false;
+  }
+  h->order_cells = (size_t)ncell;
+  return true;
+}
+
 static int enqueue(tc_handle* h, bool batch, const tcg::DevFields& f, long long ntotal, double dt, cudaStream_t st) {
   int kmode = kernel_mode(h->p.mode);
   if (h->p.mode == TC_MODE_MIXED_SEEDED || h->p.mode == TC_MODE_NEWTON_FP64_SEEDED) {
@@ -215,6 +252,14 @@ static int enqueue(tc_handle* h, bool batch, const tcg::DevFields& f, long long 
   launch_shape(h, kmode, ntotal, &grid, &block);
   if (cudaMemsetAsync(h->d_cursor, 0, sizeof(unsigned long long), st) != cudaSuccess) return TC_ECUDA;
   tcg::DevParams dp = dev_params(h->p);
+  // cost-ordered queue: only worth it when the launch holds more cells than a few warps
+  if (h->p.order_cells && ntotal > 256 && order_workspace(h, ntotal, st)) {
+    if (tcg::launch_order(batch, f, h->d_boxes, dp, dt, ntotal, h->d_okey, h->d_ohist, h->d_order, h->num_sms, st) !=
+        cudaSuccess)
+      return TC_ECUDA;
+    h->launches += 3;
+    dp.order = h->d_order;
+  }
   cudaError_t e;
   if (kmode == 0) e = tcg::launch_mode0(batch, f, h->d_boxes, dp, dt, h->d_cursor, ntotal, grid, block, st);
   else if (kmode == 1) e = tcg::launch_mode1(batch, f, h->d_boxes, dp, dt, h->d_cursor, ntotal, grid, block, st);
@@ -336,6 +381,7 @@ int tc_step_batch(tc_handle* h, const tc_fields* boxes, int nbox, double dt_s, v
       h->gexec = nullptr;
     }
     memcpy(h->h_boxes, &tb, sizeof(tb));
+    if (h->p.order_cells) order_workspace(h, tot, st);  // allocate before the capture
     cudaStream_t cap;
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return TC_ECUDA;
     cudaGraph_t g = nullptr;

@@ -649,6 +649,7 @@ __global__ void __launch_bounds__(128, step_min_blocks<MODE>()) k_step(DevFields
     if (!have) {
       long long gi = claim_cells(cursor);
       if (gi >= ntotal) break;
+      if (p.order) gi = (long long)p.order[gi];
       if (BATCH) {
         int lo = 0, hi = boxes->nbox - 1;
         while (lo < hi) {  // last box with start <= gi

@@ -75,6 +75,7 @@ struct DevParams {
   double limiter, fd_rel, rtol, rtol_mixed, T_floor;
   int newton_max, max_sub;
   unsigned flags;
+  const unsigned* order = nullptr;  // optional: the k-th claimed cell is order[k] (cost-ordered queue)
 };
 
 // ------------------------------------------------------------------ per-cell constants

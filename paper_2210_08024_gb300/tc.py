@@ -37,6 +37,7 @@ class tc_params(ctypes.Structure):
         ("newton_rtol_mixed", ctypes.c_double),
         ("block", ctypes.c_int),
         ("blocks_per_sm", ctypes.c_int),
+        ("order_cells", ctypes.c_int),
     ]
 
 
