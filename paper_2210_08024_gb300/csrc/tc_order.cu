@@ -62,13 +62,20 @@ __global__ void __launch_bounds__(128) k_order_key(DevFields f1, const BoxTable*
     s.Tmu = T0 / s.mu;
     double td = -1.0, H0, CH2, CHp;
     start_sources<double>(c, p, s, td, H0, CH2, CHp);
-    bool last;
-    const double d1 = substep_len(p, dt, c.K * s.Tmu, H0, CH2, CHp, last);
+    // r = dt / dts_1 without the cap at dt: the predicted substep count above 1, and
+    // below 1 how far the state moves within its single substep (more Newton iterations
+    // the closer r is to 1: 3.0 at r ~ 2^-10, 4.1 at r ~ 2^-1 on the slab).  Classes are
+    // quarter octaves of r from 2^-16 to 2^16.
+    const double e = c.K * s.Tmu;
+    double r = 0.0;
+    if (fabs(H0) > 0.0) r = fmax(r, fabs(H0) * dt / (p.limiter * e));
+    r = fmax(r, fabs(CH2) * dt / p.limiter);
+    r = fmax(r, fabs(CHp) * dt / p.limiter);
     int b = ORDER_BUCKETS - 1;  // unknown cost (non-finite): schedule first
-    if (d1 > 0.0 && isfinite(d1)) {
-      const double r = dt / d1;
-      b = (r > 1.0) ? (int)ceil(4.0 * log2(r)) : 0;
-      b = b < 0 ? 0 : (b > ORDER_BUCKETS - 1 ? ORDER_BUCKETS - 1 : b);
+    if (isfinite(r)) {
+      const double l = (r > 0.0) ? log2(r) : -1e30;
+      const double u = 4.0 * (l + 16.0);
+      b = (u <= 0.0) ? 0 : (u >= ORDER_BUCKETS - 1 ? ORDER_BUCKETS - 1 : (int)u);
     }
     const int k = ORDER_BUCKETS - 1 - b;  // ascending key = decreasing cost
     key[gi] = (unsigned char)k;

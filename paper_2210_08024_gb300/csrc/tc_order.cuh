@@ -6,7 +6,8 @@
 
 namespace tcg {
 
-// Cost classes: quarter-octaves of the predicted substep count dt / dts_1.
+// Cost classes: quarter octaves of dt / dts_1 (the first substep length of Sec. 6.1
+// before its cap at dt) from 2^-16 to 2^16.
 constexpr int ORDER_BUCKETS = 128;
 
 // Fills order[0..ntotal) with the cell indices (over the concatenated boxes when batch)
