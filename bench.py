@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-peaks", action="store_true", help="skip the pipe microbenchmarks (no roofline)")
+    ap.add_argument("--configs", action="store_true",
+                    help="instead of the benchmark line, time every workload config and its error vs the oracle")
     ap.add_argument("--no-drivers", action="store_true",
                     help="skip the one-zone, six-ray and PDR legs (timed after the step)")
     return ap.parse_args()
@@ -581,8 +583,101 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_configs(args):
+    """Every workload config: GPU time (CUDA events, median of 3 after a warm-up) per
+    mode, and the largest error against the oracle on sampled cells (relative on T,
+    absolute on x_H2 and x_H+).  One JSON line."""
+    import torch
+    import oracle
+    import paper_2210_08024_gb300 as P
+    from paper_2210_08024_gb300 import tc, seed_net
+    P.build()
+    blob = open(seed_net.DEFAULT_BLOB, "rb").read() if os.path.exists(seed_net.DEFAULT_BLOB) else None
+    stream = torch.cuda.current_stream()
+    ids = {"paper": tc.TC_MODE_PAPER_FP64, "newton": tc.TC_MODE_NEWTON_FP64, "mixed": tc.TC_MODE_MIXED,
+           "mixed_seeded": tc.TC_MODE_MIXED_SEEDED}
+
+    def err(g, ref):
+        return {"T_rel": float(np.max(np.abs(g["T"] - ref["T"]) / ref["T"])),
+                "x_abs": float(max(np.max(np.abs(g["xH2"] - ref["xH2"])), np.max(np.abs(g["xHp"] - ref["xHp"]))))}
+
+    def one(cells, mode, sample):
+        d = tc.to_device(cells)
+        pr = {k: d[k].clone() for k in STATE_KEYS}
+        st = tc.Stepper(ids[mode])
+        if "seeded" in mode:
+            st.load_mlp(blob)
+        f = tc.make_fields(d)
+
+        def call():
+            for k in STATE_KEYS:
+                d[k].copy_(pr[k])
+            tc.tc_step(st.h, f, DT, stream)
+        ms = _time_call(call, stream, 3)
+        idx = torch.from_numpy(sample).cuda()
+        g = {k: d[k][idx].cpu().numpy() for k in STATE_KEYS}
+        st.close()
+        return ms, g
+
+    out = {}
+    rng = np.random.default_rng(17)
+    work = [("1: 4096 random states", synthgen.cells_4096(), ("paper", "newton", "mixed"), None),
+            ("2/4: 128^3 slab", synthgen.slab(), ("newton", "mixed", "mixed_seeded"), 3000),
+            ("3: 256^3 stiff grid", synthgen.stiff(), ("mixed", "newton"), 2000)]
+    for name, cells, modes, ns in work:
+        n = cells["n"].size
+        sample = np.arange(n) if ns is None else np.sort(rng.choice(n, ns, replace=False))
+        sub = synthgen.subset(cells, sample)
+        refs = {m: oracle.step(sub, DT, oracle.default_params(mode=m)) for m in ({0} if "paper" in modes else set()) | {1}}
+        res = {"cells": n}
+        for m in modes:
+            if "seeded" in m and blob is None:
+                continue
+            ms, g = one(cells, m, sample)
+            res[m] = {"ms": ms, "cell_updates_per_s": n / (ms * 1e-3),
+                      "error_vs_oracle": err(g, refs[0 if m == "paper" else 1]),
+                      "oracle_cells_compared": int(sample.size)}
+        out[name] = res
+        torch.cuda.empty_cache()
+    # 5: 48 boxes, one batched launch replayed from a CUDA graph
+    boxes = synthgen.boxes()
+    res = {"boxes": len(boxes), "cells": int(sum(b[0]["n"].size for b in boxes))}
+    for m in ("newton", "mixed_seeded"):
+        if "seeded" in m and blob is None:
+            continue
+        devs = [tc.to_device(b[0]) for b in boxes]
+        prs = [{k: d[k].clone() for k in STATE_KEYS} for d in devs]
+        st = tc.Stepper(ids[m])
+        if "seeded" in m:
+            st.load_mlp(blob)
+        fields = [tc.make_fields(d) for d in devs]
+
+        def call():
+            for d, pr in zip(devs, prs):
+                for k in STATE_KEYS:
+                    d[k].copy_(pr[k])
+            tc.tc_step_batch(st.h, fields, DT, stream)
+        ms = _time_call(call, stream, 3)
+        worst = {"T_rel": 0.0, "x_abs": 0.0}
+        for (cells, meta), d in zip(boxes, devs):
+            idx = np.sort(rng.choice(cells["n"].size, 24, replace=False))
+            g = {k: d[k][torch.from_numpy(idx).cuda()].cpu().numpy() for k in STATE_KEYS}
+            e = err(g, oracle.step(synthgen.subset(cells, idx), DT, oracle.default_params(mode=1)))
+            worst = {k: max(worst[k], e[k]) for k in worst}
+        st.close()
+        res[m] = {"ms": ms, "cell_updates_per_s": res["cells"] / (ms * 1e-3), "error_vs_oracle": worst,
+                  "oracle_cells_compared": 24 * len(boxes), "note": "includes the state restore copies"}
+        del devs, prs, fields
+        torch.cuda.empty_cache()
+    out["5: 48 boxes, CUDA graph"] = res
+    return {"configs": out, "dt_s": DT, "data": "synthetic", "oracle": "FP64 C++ oracle on the host cores"}
+
+
 def main():
     args = parse()
+    if args.configs:
+        print(json.dumps(run_configs(args)))
+        return
     out = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if out is not None:
         print(json.dumps(out))
