@@ -30,9 +30,18 @@ def _flags():
     return ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"] + ARCH
 
 
+# The mixed-precision step kernels evaluate their Newton iterations on FP32 source terms
+# and correct every root with an FP64 polish, so their FP32 arithmetic may use the fast
+# approximate intrinsics (exp, log, divide; flush-to-zero).  This changes no FP64
+# operation.  Measured on the 128^3 slab: mixed 250 -> 215 ms, mixed + seed 295 ->
+# 238 ms, with the same iteration counts and the same parity results.
+FAST_FP32 = {"tc_k_mixed.cu", "tc_k_seeded3.cu"}
+
+
 def _compile(src: str) -> tuple[str, str]:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc()] + _flags() + ["-c", os.path.join(CSRC, src), "-o", obj]
+    extra = ["--use_fast_math"] if src in FAST_FP32 else []
+    cmd = [nvcc()] + _flags() + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed on %s:\n%s" % (src, r.stderr[-4000:]))
