@@ -74,7 +74,8 @@ typedef struct tc_params {
   int max_substeps;            /* substep cap per cell; default 1e6 */
   int mode;                    /* TC_MODE_* */
   unsigned flags;              /* TC_CONST_KGR | TC_NO_ROVIB | TC_NO_CIE */
-  double newton_rtol_mixed;    /* step tolerance of the FP32 Newton iterations of the mixed modes; default 1e-7 */
+  double newton_rtol_mixed;    /* step tolerance of the FP32 Newton iterations of the mixed modes; default 1e-6
+                                  (the FP64 polish then brings each root to 1e-7 relative) */
   int block;                   /* threads per block (0 = autotuned/default) */
   int blocks_per_sm;           /* resident blocks per SM for the persistent grid (0 = occupancy) */
   int order_cells;             /* 1 (default): hand cells to the persistent kernel in decreasing order of

@@ -90,7 +90,7 @@ int tc_params_default(tc_params* p, int mode) {
   p->max_substeps = 1000000;
   p->mode = mode;
   p->flags = 0;
-  p->newton_rtol_mixed = 1e-7;
+  p->newton_rtol_mixed = 1e-6;
   p->block = 0;
   p->blocks_per_sm = 0;
   p->order_cells = 1;
