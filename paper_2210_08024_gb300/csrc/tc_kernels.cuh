@@ -571,10 +571,15 @@ TCG_FN void substep_mixed(const CellC<double>& c, const CellC<float>& cf, const 
 }
 
 // ------------------------------------------------------------------ seeding (modes 3, 4)
+// Activations of the in-kernel seed inference are stored in FP16: the seed needs ~1e-2
+// accuracy, and half-size buffers let 4 blocks of 128 threads share an SM (~52 KB each)
+// instead of 2.
+using seed_act_t = __half;
+
 // Shared-memory footprint of the seeded kernels for `block` threads: the weights and
 // two [64][block] activation buffers.
 __host__ __device__ constexpr size_t seed_smem_bytes(int block) {
-  return sizeof(MlpDev) + 2 * (size_t)MLP_HID * block * sizeof(float);
+  return sizeof(MlpDev) + 2 * (size_t)MLP_HID * block * sizeof(seed_act_t);
 }
 
 // Seed of a substep's Newton iteration from the network: features of the substep start
@@ -584,7 +589,7 @@ __host__ __device__ constexpr size_t seed_smem_bytes(int block) {
 // (T_mu, x_H2, x_H+) with mu frozen at the substep start and clamped inside the
 // admissible region.  Returns
 // false (no seed) if the prediction is not finite.
-TCG_FN bool mlp_seed(const MlpDev* w, float* buf0, float* buf1, int st, const float* lf, const LaneState& s,
+TCG_FN bool mlp_seed(const MlpDev* w, seed_act_t* buf0, seed_act_t* buf1, int st, const float* lf, const LaneState& s,
                      double dts, const DevParams& p, double* seed) {
   const double T0 = s.mu * s.Tmu;
   float f[MLP_IN] = {lf[0], (float)log10(T0), (float)s.xH2, (float)s.xHp, lf[1], lf[2], lf[3], lf[4],
@@ -609,21 +614,19 @@ TCG_FN bool mlp_seed(const MlpDev* w, float* buf0, float* buf1, int st, const fl
 // Registers: 128 threads per block and at least 4 resident blocks per SM (128 registers
 // per thread, some spilled to L1) measured faster than the 168 registers and 3 blocks
 // the compiler picks on its own: 510 vs 546 ms (FP64 Newton) and 352 vs 403 ms (mixed)
-// on the 128^3 slab.  The seeded modes keep 2 blocks: their shared-memory weights and
-// activations (~84 KB per block) allow no more.
-template <int MODE>
-constexpr int step_min_blocks() { return (MODE == 3 || MODE == 4) ? 2 : 4; }
+// on the 128^3 slab.  The seeded modes fit 4 blocks too (~52 KB of shared memory each).
+constexpr int STEP_MIN_BLOCKS = 4;
 
 template <int MODE, bool BATCH>
-__global__ void __launch_bounds__(128, step_min_blocks<MODE>()) k_step(DevFields f1, const BoxTable* __restrict__ boxes, DevParams p,
+__global__ void __launch_bounds__(128, STEP_MIN_BLOCKS) k_step(DevFields f1, const BoxTable* __restrict__ boxes, DevParams p,
                                                double dt, unsigned long long* cursor, long long ntotal,
                                                const MlpDev* __restrict__ mlp) {
   constexpr bool SEEDED = (MODE == 3 || MODE == 4);
   constexpr bool MIXED = (MODE == 2 || MODE == 3);
   extern __shared__ __align__(16) unsigned char smem[];
   const MlpDev* wsm = nullptr;
-  float* buf0 = nullptr;
-  float* buf1 = nullptr;
+  seed_act_t* buf0 = nullptr;
+  seed_act_t* buf1 = nullptr;
   if constexpr (SEEDED) {
     // weights to shared memory once per block
     const int4* src = reinterpret_cast<const int4*>(mlp);
@@ -631,7 +634,7 @@ __global__ void __launch_bounds__(128, step_min_blocks<MODE>()) k_step(DevFields
     for (int i = threadIdx.x; i < (int)(sizeof(MlpDev) / 16); i += blockDim.x) dst[i] = src[i];
     __syncthreads();
     wsm = reinterpret_cast<const MlpDev*>(smem);
-    float* act = reinterpret_cast<float*>(smem + sizeof(MlpDev));
+    seed_act_t* act = reinterpret_cast<seed_act_t*>(smem + sizeof(MlpDev));
     buf0 = act + threadIdx.x;
     buf1 = act + (size_t)MLP_HID * blockDim.x + threadIdx.x;
   }

@@ -10,6 +10,7 @@
 // Weights are BF16, everything else FP32; sums accumulate in FP32.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -47,11 +48,17 @@ TCG_MLP_FN float mlp_silu(float z) {
 #endif
 }
 
+// Activation storage: FP32, or FP16 where shared memory is short (the step kernel).
+TCG_MLP_FN float act_load(const float* p) { return *p; }
+TCG_MLP_FN void act_store(float* p, float v) { *p = v; }
+TCG_MLP_FN float act_load(const __half* p) { return __half2float(*p); }
+TCG_MLP_FN void act_store(__half* p, float v) { *p = __float2half(v); }
+
 // One hidden layer for this thread: out[j] = silu(b[j] + sum_k Wt[k][j] in[k]), with
 // in and out in shared memory at stride `st` (one column per thread of the block).
-template <int K>
+template <int K, class A>
 TCG_MLP_FN void mlp_layer(const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ b,
-                                          const float* in, float* out, int st) {
+                                          const A* in, A* out, int st) {
 #pragma unroll 1
   for (int j0 = 0; j0 < MLP_HID; j0 += 16) {
     float acc[16];
@@ -59,7 +66,7 @@ TCG_MLP_FN void mlp_layer(const __nv_bfloat16* __restrict__ Wt, const float* __r
     for (int jj = 0; jj < 16; ++jj) acc[jj] = b[j0 + jj];
 #pragma unroll 4
     for (int k = 0; k < K; ++k) {
-      const float a = in[k * st];
+      const float a = act_load(in + k * st);
       const __nv_bfloat162* w2 = reinterpret_cast<const __nv_bfloat162*>(Wt + k * MLP_HID + j0);
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
@@ -69,23 +76,23 @@ TCG_MLP_FN void mlp_layer(const __nv_bfloat16* __restrict__ Wt, const float* __r
       }
     }
 #pragma unroll
-    for (int jj = 0; jj < 16; ++jj) out[(j0 + jj) * st] = mlp_silu(acc[jj]);
+    for (int jj = 0; jj < 16; ++jj) act_store(out + (j0 + jj) * st, mlp_silu(acc[jj]));
   }
 }
 
 // Network output for raw features f[9].  `w` points to the weights in shared memory;
-// buf0/buf1 point to this thread's column of two [64][st] float buffers.
-TCG_MLP_FN void mlp_infer(const MlpDev* w, float* buf0, float* buf1, int st, const float* f,
-                                          float* o) {
+// buf0/buf1 point to this thread's column of two [64][st] activation buffers.
+template <class A>
+TCG_MLP_FN void mlp_infer(const MlpDev* w, A* buf0, A* buf1, int st, const float* f, float* o) {
 #pragma unroll
-  for (int k = 0; k < MLP_IN; ++k) buf1[k * st] = (f[k] - w->in_mean[k]) * w->in_inv_std[k];
+  for (int k = 0; k < MLP_IN; ++k) act_store(buf1 + k * st, (f[k] - w->in_mean[k]) * w->in_inv_std[k]);
   mlp_layer<MLP_IN>(w->W1t, w->b1, buf1, buf0, st);
   mlp_layer<MLP_HID>(w->W2t, w->b2, buf0, buf1, st);
   mlp_layer<MLP_HID>(w->W3t, w->b3, buf1, buf0, st);
   float a0 = w->b4[0], a1 = w->b4[1], a2 = w->b4[2];
 #pragma unroll 8
   for (int k = 0; k < MLP_HID; ++k) {
-    const float h = buf0[k * st];
+    const float h = act_load(buf0 + k * st);
     a0 = fmaf(__bfloat162float(w->W4t[k * 4 + 0]), h, a0);
     a1 = fmaf(__bfloat162float(w->W4t[k * 4 + 1]), h, a1);
     a2 = fmaf(__bfloat162float(w->W4t[k * 4 + 2]), h, a2);
