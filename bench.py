@@ -518,7 +518,9 @@ def roofline_of(work, r, mode, ncell, peaks):
             "work": "FP64 flops of the library's step per cell (work_slab128.json, %s) x %d cells" %
                     (MODE_WORK[mode], ncell),
             "kernel": "k_step<%d,false>" % {"paper": 0, "newton": 1, "mixed": 2, "mixed_seeded": 3,
-                                             "newton_seeded": 4}[mode]}
+                                             "newton_seeded": 4}[mode],
+            "timed": "one tc_step: the three cost-ordering kernels (~2%) and the step kernel, CUDA events "
+                     "on the launching stream"}
 
 
 def oracle_sample(cells, head, budget_s=15.0):
