@@ -583,8 +583,8 @@ __host__ __device__ constexpr size_t seed_smem_bytes(int block) {
 }
 
 // Seed of a substep's Newton iteration from the network: features of the substep start
-// (state, per-cell field features lf[5] = log10 n, log10 chi_FUV, log10 f_shld,H2,
-// log10(F_LyC+1), log10 xi) and its length; the outputs are the predicted changes of
+// (state, per-cell features lf[6] = log10 n, log10 chi_FUV, log10 f_shld,H2,
+// log10(F_LyC+1), log10 xi, log10 Z'_d) and its length; the outputs are the predicted changes of
 // x_H2 (/0.5), x_H+ and log10 T over the substep's backward-Euler step, mapped to
 // (T_mu, x_H2, x_H+) with mu frozen at the substep start and clamped inside the
 // admissible region.  Returns
@@ -593,7 +593,7 @@ TCG_FN bool mlp_seed(const MlpDev* w, seed_act_t* buf0, seed_act_t* buf1, int st
                      double dts, const DevParams& p, double* seed) {
   const double T0 = s.mu * s.Tmu;
   float f[MLP_IN] = {lf[0], (float)log10(T0), (float)s.xH2, (float)s.xHp, lf[1], lf[2], lf[3], lf[4],
-                     (float)log10(dts)};
+                     (float)log10(dts), lf[5]};
   float o[MLP_OUT];
   mlp_infer(w, buf0, buf1, st, f, o);
   if (!(isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]))) return false;
@@ -638,7 +638,7 @@ __global__ void __launch_bounds__(128, STEP_MIN_BLOCKS) k_step(DevFields f1, con
     buf0 = act + threadIdx.x;
     buf1 = act + (size_t)MLP_HID * blockDim.x + threadIdx.x;
   }
-  float lf[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  float lf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   LaneState s;
   CellC<double> c;
   CellC<float> cf;   // FP32 copy of the cell constants (mixed modes)
@@ -695,6 +695,7 @@ __global__ void __launch_bounds__(128, STEP_MIN_BLOCKS) k_step(DevFields f1, con
         lf[2] = (float)log10(fmax(fb.fh2[li], 1e-30));
         lf[3] = (float)log10(Fl + 1.0);
         lf[4] = (float)log10(fmax(fb.xi[li], 1e-30));
+        lf[5] = (float)log10(fmax(fb.Zd ? fb.Zd[li] : fb.Zd_val, 1e-30));
       }
       s.mu = c.muH / (1.1 + s.xe - x20);
       s.Tmu = T0 / s.mu;

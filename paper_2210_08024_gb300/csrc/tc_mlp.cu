@@ -1,7 +1,7 @@
 // Training of the seed network on the GPU (declared in include/tc_mlp.h).
 //
 // Parameters live on the device as one FP32 master vector in the order
-//   W1[64][9], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[3][64], b4[3]
+//   W1[64][10], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[3][64], b4[3]
 // (weights [out][in]).  The forward and backward passes use the weights rounded to
 // BF16, as the step kernel's inference does, and accumulate in FP32.  The weight
 // gradient of the BF16 network is applied to the FP32 masters by Adam.
@@ -29,7 +29,7 @@ using tcg::MLP_HID;
 using tcg::MLP_IN;
 using tcg::MLP_OUT;
 
-constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + 64 * 9, OFF_W2 = OFF_B1 + 64, OFF_B2 = OFF_W2 + 64 * 64,
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + 64 * MLP_IN, OFF_W2 = OFF_B1 + 64, OFF_B2 = OFF_W2 + 64 * 64,
               OFF_W3 = OFF_B2 + 64, OFF_B3 = OFF_W3 + 64 * 64, OFF_W4 = OFF_B3 + 64, OFF_B4 = OFF_W4 + 3 * 64,
               NPARAM = OFF_B4 + 3;
 
@@ -128,7 +128,7 @@ struct tc_mlp {
   float* grad = nullptr;
   float* m = nullptr;
   float* v = nullptr;
-  float* norm = nullptr;   // mean[9], inv_std[9]
+  float* norm = nullptr;   // mean[MLP_IN], inv_std[MLP_IN]
   float* loss = nullptr;
   float* work = nullptr;   // activations for cap samples
   int cap = 0;
@@ -138,7 +138,7 @@ struct tc_mlp {
 
 namespace {
 
-// Work layout for B samples: A0[B*9] Z1 H1 Z2 H2 Z3 H3 [B*64 each] O G[B*3] G3 G2 G1 [B*64].
+// Work layout for B samples: A0[B*MLP_IN] Z1 H1 Z2 H2 Z3 H3 [B*64 each] O G[B*3] G3 G2 G1 [B*64].
 size_t work_floats(int B) { return (size_t)B * (MLP_IN + 6 * MLP_HID + 2 * MLP_OUT + 3 * MLP_HID); }
 
 int ensure_cap(tc_mlp* h, int B) {
@@ -251,7 +251,7 @@ int tc_mlp_create(unsigned long long seed, tc_mlp** out) {
       th[off + i] = (float)((2.0 * u - 1.0) * bound);
     }
   };
-  fill(OFF_W1, 64, 9);
+  fill(OFF_W1, 64, MLP_IN);
   fill(OFF_W2, 64, 64);
   fill(OFF_W3, 64, 64);
   fill(OFF_W4, 3, 64);

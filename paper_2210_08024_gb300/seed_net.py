@@ -39,12 +39,12 @@ DEFAULT_BLOB = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights
 
 
 def features(cells: dict, T, xH2, xHp, dt) -> np.ndarray:
-    """Raw (unnormalised) features in the order of include/tc_mlp.h, float32 [N, 9]."""
+    """Raw (unnormalised) features in the order of include/tc_mlp.h, float32 [N, 10]."""
     n = np.asarray(cells["n"], dtype=np.float64)
     N = n.size
     bc = lambda v: np.broadcast_to(np.asarray(v, dtype=np.float64), (N,))  # noqa: E731
     chi_fuv = (1.8e-4 * bc(cells["chi_pe"]) + 3.0e-5 * bc(cells["chi_lw"])) / 2.1e-4
-    X = np.empty((N, 9), dtype=np.float32)
+    X = np.empty((N, 10), dtype=np.float32)
     X[:, 0] = np.log10(n)
     X[:, 1] = np.log10(bc(T))
     X[:, 2] = bc(xH2)
@@ -54,6 +54,7 @@ def features(cells: dict, T, xH2, xHp, dt) -> np.ndarray:
     X[:, 6] = np.log10(bc(cells["F_lyc"]) + 1.0)
     X[:, 7] = np.log10(np.maximum(bc(cells["xi"]), 1e-30))
     X[:, 8] = np.log10(bc(dt))
+    X[:, 9] = np.log10(np.maximum(bc(cells["Zd"]), 1e-30))
     return X
 
 

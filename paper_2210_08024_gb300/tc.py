@@ -464,7 +464,7 @@ def _f32(a):
 
 class SeedNet:
     """Handle of the seed network (include/tc_mlp.h).  X, Y are device float32 torch
-    tensors of shape [B, 9] and [B, 3]; all arithmetic runs in the library's kernels."""
+    tensors of shape [B, 10] and [B, 3]; all arithmetic runs in the library's kernels."""
 
     def __init__(self, seed: int = 0):
         self.h = ctypes.c_void_p()

@@ -41,14 +41,14 @@ def _random_net(tc, seed=0):
     theta = (g.normal(0.0, 0.25, ref_mlp.n_params())).astype(np.float32)
     net = tc.SeedNet(1)
     net.set_params(theta)
-    net.set_norm(np.zeros(9), np.ones(9))
+    net.set_norm(np.zeros(ref_mlp.N_IN), np.ones(ref_mlp.N_IN))
     return net, theta.astype(np.float64)
 
 
 def test_forward_matches_fp64_reference(tc):
     import torch
     net, theta = _random_net(tc)
-    x = np.random.default_rng(1).normal(0, 1, (1000, 9)).astype(np.float32)
+    x = np.random.default_rng(1).normal(0, 1, (1000, ref_mlp.N_IN)).astype(np.float32)
     o = net.predict(torch.from_numpy(x).cuda()).cpu().numpy()
     r, _, _ = ref_mlp.forward(_rounded(theta), x.astype(np.float64))
     np.testing.assert_allclose(o, r, rtol=1e-4, atol=1e-5)
@@ -59,7 +59,7 @@ def test_gradient_matches_fp64_reference(tc):
     import torch
     net, theta = _random_net(tc, 2)
     g = np.random.default_rng(3)
-    x = g.normal(0, 1, (4096, 9)).astype(np.float32)
+    x = g.normal(0, 1, (4096, ref_mlp.N_IN)).astype(np.float32)
     y = g.normal(0, 1, (4096, 3)).astype(np.float32)
     w = (1.0, 2.0, 0.5)
     grad, loss = net.grad(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), w)
@@ -82,7 +82,7 @@ def test_gradient_matches_fp64_reference(tc):
 def test_training_reduces_loss(tc):
     import torch
     g = np.random.default_rng(4)
-    x = g.normal(0, 1, (16384, 9)).astype(np.float32)
+    x = g.normal(0, 1, (16384, ref_mlp.N_IN)).astype(np.float32)
     y = np.stack([np.tanh(x[:, 0] - x[:, 1]), 0.5 * x[:, 2] * x[:, 3], np.sin(x[:, 4])], axis=1).astype(np.float32)
     net = tc.SeedNet(5)
     X, Y = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()

@@ -17,7 +17,7 @@ def _rand(seed=0, B=7):
 
 
 def test_param_count_and_layout():
-    assert mlp.n_params() == 64 * 9 + 64 + 2 * (64 * 64 + 64) + 3 * 64 + 3
+    assert mlp.n_params() == 64 * 10 + 64 + 2 * (64 * 64 + 64) + 3 * 64 + 3
     theta, _, _ = _rand()
     assert np.array_equal(mlp.flatten(mlp.unflatten(theta)), theta)
 
@@ -49,7 +49,7 @@ def test_degenerate_networks():
     W = [np.zeros(s) for s in mlp.SHAPES]
     W[7] = np.array([0.3, -0.2, 1.5])
     theta = mlp.flatten(W)
-    x = np.random.default_rng(3).normal(size=(5, 9))
+    x = np.random.default_rng(3).normal(size=(5, mlp.N_IN))
     o, _, _ = mlp.forward(theta, x)
     np.testing.assert_allclose(o, np.tile(W[7], (5, 1)), rtol=0, atol=0)
     # with zero hidden biases and zero W1 every hidden unit is silu(0) = 0, so the
