@@ -74,6 +74,30 @@ def dist_env():
     return ws, rank, local
 
 
+# ----- multi-rank host logic (one process per GPU; cells are independent, so each rank
+# advances its own slab and the only collectives are the timing barrier and reduction)
+def workload_key(rank: int) -> int:
+    """Seed key of the slab a rank advances: every rank gets a different slab."""
+    return 2 + rank
+
+
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    """The largest x over the ranks: the job's time is its slowest rank's."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ncell_per_rank: int, ws: int, steps: int, ms: float) -> float:
+    """Cell-updates per second of the whole job: every rank's cells over the slowest
+    rank's time (weak scaling)."""
+    return ws * ncell_per_rank * steps / (ms * 1e-3)
+
+
 def work_per_cell():
     """FP64 operations per cell by class (add, mul, div, sqrt, exp, log) of one step on
     the slab, per mode, counted from the library's own step functions
@@ -187,7 +211,7 @@ def run_gpu(args):
             import torch.distributed as dist
             dist.barrier()
 
-    cells = synthgen.slab(side=args.side, key=2 + rank)
+    cells = synthgen.slab(side=args.side, key=workload_key(rank))
     ncell = int(cells["n"].size)
     dev = tc.to_device(cells)
     pristine = {k: dev[k].clone() for k in STATE_KEYS}
@@ -238,14 +262,10 @@ def run_gpu(args):
         ms = t0.elapsed_time(t1)
         kms = [a.elapsed_time(b) for a, b in kev]
         launches = st.launches() - l0
-        if ws > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(ms, ws, "cuda")
         nbad = tc.tc_sync_status(st.h, dev["status"])
         results[mname] = {"ms_per_step": ms / args.steps, "kernel_ms": float(np.mean(kms)),
-                          "value": ws * ncell * args.steps / (ms * 1e-3), "launches": launches,
+                          "value": job_throughput(ncell, ws, args.steps, ms), "launches": launches,
                           "cells_not_ok": nbad, "newton_iters_per_cell": float(dev["iters"].double().mean().item()),
                           "mode_id": mode_ids[mname]}
         st.close()
@@ -464,13 +484,9 @@ def run_e2e(args, tc, torch, cells, ncell, mode_id, stream, barrier, ws):
         tc.tc_step_host(st.h, hf, DT, stream)  # copies in, runs, copies out, synchronises
         e2e_ms += (time.perf_counter() - a) * 1e3
     barrier()
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e2e_ms, ws, "cuda")
     st.close()
-    return {"value": ws * ncell * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+    return {"value": job_throughput(ncell, ws, args.steps, e2e_ms), "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "api": "tc_step_host"}
 
 
