@@ -602,9 +602,9 @@ def run_reference(args):
 
 
 def run_configs(args):
-    """Every workload config: GPU time (CUDA events, median of 3 after a warm-up) per
-    mode, and the largest error against the oracle on sampled cells (relative on T,
-    absolute on x_H2 and x_H+).  One JSON line."""
+    """Every workload config: GPU time (CUDA events, median of 3 after a warm-up; the
+    48-box sweep one call after the warm-up) per mode, and the largest error against the
+    oracle on sampled cells (relative on T, absolute on x_H2 and x_H+).  One JSON line."""
     import torch
     import oracle
     import paper_2210_08024_gb300 as P
@@ -675,7 +675,7 @@ def run_configs(args):
                 for k in STATE_KEYS:
                     d[k].copy_(pr[k])
             tc.tc_step_batch(st.h, fields, DT, stream)
-        ms = _time_call(call, stream, 3)
+        ms = _time_call(call, stream, 1)   # ~2 min per call: one timed call after the warm-up
         worst = {"T_rel": 0.0, "x_abs": 0.0}
         for (cells, meta), d in zip(boxes, devs):
             idx = np.sort(rng.choice(cells["n"].size, 24, replace=False))
