@@ -611,14 +611,19 @@ TCG_FN bool mlp_seed(const MlpDev* w, seed_act_t* buf0, seed_act_t* buf1, int st
 }
 
 // ------------------------------------------------------------------ the kernel
-// Registers: 128 threads per block and at least 4 resident blocks per SM (128 registers
-// per thread, some spilled to L1) measured faster than the 168 registers and 3 blocks
-// the compiler picks on its own: 510 vs 546 ms (FP64 Newton) and 352 vs 403 ms (mixed)
-// on the 128^3 slab.  The seeded modes fit 4 blocks too (~52 KB of shared memory each).
-constexpr int STEP_MIN_BLOCKS = 4;
+// Registers: 128 threads per block and at least 8 resident blocks per SM (64 registers
+// per thread, the rest spilled to L1) for the unseeded modes.  More resident warps hide
+// more of the latency of these long dependent FP64 chains than the spills cost.
+// Measured on the 128^3 slab (FP64 Newton / mixed, ms):
+//   3 blocks (168 registers, compiler's choice) 546 / 403
+//   4 blocks (128) 394 / 195,  5 (96) 375 / 174,  6 (80) 365 / 164,
+//   7 (72) 362 / 156,  8 (64) 363 / 152.
+// The seeded modes keep 4: their shared memory (~52 KB per block) allows no more.
+template <int MODE>
+constexpr int step_min_blocks() { return (MODE == 3 || MODE == 4) ? 4 : 8; }
 
 template <int MODE, bool BATCH>
-__global__ void __launch_bounds__(128, STEP_MIN_BLOCKS) k_step(DevFields f1, const BoxTable* __restrict__ boxes, DevParams p,
+__global__ void __launch_bounds__(128, step_min_blocks<MODE>()) k_step(DevFields f1, const BoxTable* __restrict__ boxes, DevParams p,
                                                double dt, unsigned long long* cursor, long long ntotal,
                                                const MlpDev* __restrict__ mlp) {
   constexpr bool SEEDED = (MODE == 3 || MODE == 4);
