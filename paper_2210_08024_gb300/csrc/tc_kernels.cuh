@@ -571,16 +571,9 @@ TCG_FN void substep_mixed(const CellC<double>& c, const CellC<float>& cf, const 
 }
 
 // ------------------------------------------------------------------ seeding (modes 3, 4)
-// Activations of the in-kernel seed inference are stored in FP16: the seed needs ~1e-2
-// accuracy, and half-size buffers let 4 blocks of 128 threads share an SM (~52 KB each)
-// instead of 2.
+// Activations of the in-kernel seed inference are stored in FP16 (the seed needs ~1e-2
+// accuracy): 256 bytes of per-thread local memory instead of 512.
 using seed_act_t = __half;
-
-// Shared-memory footprint of the seeded kernels for `block` threads: the weights and
-// two [64][block] activation buffers.
-__host__ __device__ constexpr size_t seed_smem_bytes(int block) {
-  return sizeof(MlpDev) + 2 * (size_t)MLP_HID * block * sizeof(seed_act_t);
-}
 
 // Seed of a substep's Newton iteration from the network: features of the substep start
 // (state, per-cell features lf[6] = log10 n, log10 chi_FUV, log10 f_shld,H2,
@@ -589,7 +582,8 @@ __host__ __device__ constexpr size_t seed_smem_bytes(int block) {
 // (T_mu, x_H2, x_H+) with mu frozen at the substep start and clamped inside the
 // admissible region.  Returns
 // false (no seed) if the prediction is not finite.
-TCG_FN bool mlp_seed(const MlpDev* w, seed_act_t* buf0, seed_act_t* buf1, int st, const float* lf, const LaneState& s,
+TCG_FN bool mlp_seed(const MlpDev* __restrict__ w, seed_act_t* buf0, seed_act_t* buf1, int st, const float* lf,
+                     const LaneState& s,
                      double dts, const DevParams& p, double* seed) {
   const double T0 = s.mu * s.Tmu;
   float f[MLP_IN] = {lf[0], (float)log10(T0), (float)s.xH2, (float)s.xHp, lf[1], lf[2], lf[3], lf[4],
@@ -612,36 +606,33 @@ TCG_FN bool mlp_seed(const MlpDev* w, seed_act_t* buf0, seed_act_t* buf1, int st
 
 // ------------------------------------------------------------------ the kernel
 // Registers: 128 threads per block and at least 8 resident blocks per SM (64 registers
-// per thread, the rest spilled to L1) for the unseeded modes.  More resident warps hide
-// more of the latency of these long dependent FP64 chains than the spills cost.
-// Measured on the 128^3 slab (FP64 Newton / mixed, ms):
+// per thread, the rest spilled to L1).  More resident warps hide more of the latency of
+// these long dependent FP64 chains than the spills cost.  Measured on the 128^3 slab
+// (FP64 Newton / mixed, ms):
 //   3 blocks (168 registers, compiler's choice) 546 / 403
 //   4 blocks (128) 394 / 195,  5 (96) 375 / 174,  6 (80) 365 / 164,
 //   7 (72) 362 / 156,  8 (64) 363 / 152.
-// The seeded modes keep 4: their shared memory (~52 KB per block) allows no more.
-template <int MODE>
-constexpr int step_min_blocks() { return (MODE == 3 || MODE == 4) ? 4 : 8; }
+constexpr int STEP_MIN_BLOCKS = 8;
 
 template <int MODE, bool BATCH>
-__global__ void __launch_bounds__(128, step_min_blocks<MODE>()) k_step(DevFields f1, const BoxTable* __restrict__ boxes, DevParams p,
+__global__ void __launch_bounds__(128, STEP_MIN_BLOCKS) k_step(DevFields f1, const BoxTable* __restrict__ boxes, DevParams p,
                                                double dt, unsigned long long* cursor, long long ntotal,
                                                const MlpDev* __restrict__ mlp) {
   constexpr bool SEEDED = (MODE == 3 || MODE == 4);
   constexpr bool MIXED = (MODE == 2 || MODE == 3);
-  extern __shared__ __align__(16) unsigned char smem[];
   const MlpDev* wsm = nullptr;
   seed_act_t* buf0 = nullptr;
   seed_act_t* buf1 = nullptr;
+  // Seed network: the lanes of a warp read the same weight at the same time, so the
+  // weights are read from global memory through L1 (a broadcast) rather than copied to
+  // shared memory; the activations are per-thread arrays.  With no shared memory the
+  // seeded kernels hold as many blocks per SM as the others (136 vs 183 ms for seeded
+  // mixed on the 128^3 slab, against weights and activations in shared memory).
+  seed_act_t act_local[SEEDED ? 2 * MLP_HID : 1];
   if constexpr (SEEDED) {
-    // weights to shared memory once per block
-    const int4* src = reinterpret_cast<const int4*>(mlp);
-    int4* dst = reinterpret_cast<int4*>(smem);
-    for (int i = threadIdx.x; i < (int)(sizeof(MlpDev) / 16); i += blockDim.x) dst[i] = src[i];
-    __syncthreads();
-    wsm = reinterpret_cast<const MlpDev*>(smem);
-    seed_act_t* act = reinterpret_cast<seed_act_t*>(smem + sizeof(MlpDev));
-    buf0 = act + threadIdx.x;
-    buf1 = act + (size_t)MLP_HID * blockDim.x + threadIdx.x;
+    wsm = mlp;
+    buf0 = act_local;
+    buf1 = act_local + MLP_HID;
   }
   float lf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   LaneState s;
@@ -720,7 +711,7 @@ __global__ void __launch_bounds__(128, step_min_blocks<MODE>()) k_step(DevFields
         bool last;
         const double dts = substep_start64(c, p, dt, s, (MODE == 3) ? td64 : td_g, last);
         double seed[3];
-        const bool ok = mlp_seed(wsm, buf0, buf1, blockDim.x, lf, s, dts, p, seed);
+        const bool ok = mlp_seed(wsm, buf0, buf1, 1, lf, s, dts, p, seed);
         if constexpr (MODE == 3) substep_mixed_solve(c, cf, p, dt, dts, last, s, xe_gf, td_gf, td64, ok ? seed : nullptr);
         else solve_substep64(c, p, dt, dts, last, s, xe_g, td_g, ok ? seed : nullptr);
       }

@@ -57,7 +57,7 @@ TCG_MLP_FN float act_load(const __half* p) { return __half2float(*p); }
 TCG_MLP_FN void act_store(__half* p, float v) { *p = __float2half(v); }
 
 // One hidden layer for this thread: out[j] = silu(b[j] + sum_k Wt[k][j] in[k]), with
-// in and out in shared memory at stride `st` (one column per thread of the block).
+// in[k] at in + k * st and out[j] at out + j * st.
 template <int K, class A>
 TCG_MLP_FN void mlp_layer(const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ b,
                                           const A* in, A* out, int st) {
@@ -82,8 +82,8 @@ TCG_MLP_FN void mlp_layer(const __nv_bfloat16* __restrict__ Wt, const float* __r
   }
 }
 
-// Network output for raw features f[10].  `w` points to the weights in shared memory;
-// buf0/buf1 point to this thread's column of two [64][st] activation buffers.
+// Network output for raw features f[10].  `w` points to the weights; buf0/buf1 point
+// to this thread's two activation buffers of 64 entries at stride `st`.
 template <class A>
 TCG_MLP_FN void mlp_infer(const MlpDev* w, A* buf0, A* buf1, int st, const float* f, float* o) {
 #pragma unroll
