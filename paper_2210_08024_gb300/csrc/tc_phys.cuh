@@ -9,9 +9,9 @@
 // Powers of T and psi are taken as exp(c ln T), exp(c ln psi) from one logarithm.
 //
 // F is double for the FP64 paths and float for the mixed path's source terms.  Terms
-// the paper names but does not print use the closure definitions listed in the
-// library's closure registry: the same definitions as the CPU checker,
-// written independently here.
+// the paper names but does not print (closures: cited fits and tables it does not
+// reproduce) use one stated definition each, labelled where it is a stand-in for the
+// cited source; the CPU checker uses the same definitions, written independently.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
