@@ -276,6 +276,7 @@ def run_gpu(args):
 
     head = modes[0]
     e2e = None if args.no_e2e else run_e2e(args, tc, torch, cells, ncell, mode_ids[head], stream, barrier, ws)
+    hint = None if (args.no_drivers or rank != 0) else run_hint(args, tc, torch, stream, cells)
     drivers = None
     if rank == 0 and not args.no_drivers:
         drivers = {"onezone": run_onezone(args, tc, torch, stream), "sixray": run_sixray(args, tc, torch, stream, peaks),
@@ -287,7 +288,37 @@ def run_gpu(args):
         return None
     out = report(args, results, head, ncell, peaks, e2e, clocks, cells, ws)
     out["drivers"] = drivers
+    out["second_step_cost_hint"] = hint
     return out
+
+
+def run_hint(args, tc, torch, stream, cells):
+    """A second step of the slab, from the state the first one produced, ordered either
+    by the predicted substep count or by the first step's Newton iterations as a cost
+    hint (tc_fields.cost_hint): what a simulation calling the library every step gets."""
+    out = {}
+    for mname, mode in (("newton", tc.TC_MODE_NEWTON_FP64), ("mixed", tc.TC_MODE_MIXED)):
+        d = tc.to_device(cells)
+        st = tc.Stepper(mode)
+        st.step(d, DT, stream)
+        torch.cuda.synchronize()
+        start = {k: d[k].clone() for k in STATE_KEYS}
+        prev_iters = d["iters"].clone()
+        res = {}
+        for name, hint in (("predicted", None), ("previous_step_iterations", prev_iters)):
+            d["cost_hint"] = hint
+            f = tc.make_fields(d)
+
+            def call():
+                for k in STATE_KEYS:
+                    d[k].copy_(start[k])
+                tc.tc_step(st.h, f, DT, stream)
+            res[name] = _time_call(call, stream, 3)
+        st.close()
+        res["unit"] = "ms per step"
+        out[mname] = res
+    return out
+
 
 
 def _time_call(fn, stream, reps, flush=None):

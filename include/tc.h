@@ -106,6 +106,12 @@ typedef struct tc_fields {
   double Zg_val, Zd_val;    /* scalars used when Zg / Zd are NULL */
   int *newton_iters;        /* optional out (device, may be NULL): Newton iterations summed over the
                                cell's substeps (modes 1-4; the mixed modes count FP32 iterations) */
+  const int *cost_hint;     /* optional in (device, may be NULL; tc_step and tc_step_batch only): a
+                               per-cell cost estimate, larger = costlier, for example the newton_iters
+                               output of the cell's previous step.  With tc_params.order_cells set,
+                               cells are claimed in decreasing order of the hint instead of the
+                               predicted substep count (in a simulation consecutive steps of a cell
+                               cost about the same).  Results do not depend on it. */
 } tc_fields;
 
 typedef struct tc_handle tc_handle;

@@ -170,6 +170,7 @@ static int check_fields(const tc_fields* f) {
   const void* opt[] = {f->f_shld_c, f->F_lyc, f->Zg, f->Zd, f->x_e, f->x_cp, f->x_co};
   for (const void* q : opt)
     if (q && !aligned8(q)) return TC_EINVAL;
+  if (f->cost_hint && (((uintptr_t)f->cost_hint) & 3u)) return TC_EINVAL;
   if (!f->Zg && !(f->Zg_val >= 0.0)) return TC_EINVAL;
   if (!f->Zd && !(f->Zd_val >= 0.0)) return TC_EINVAL;
   return TC_OK;
@@ -181,6 +182,7 @@ static tcg::DevFields dev_fields(const tc_fields* f) {
   d.Flyc = f->F_lyc; d.xi = f->xi_cr; d.Zg = f->Zg; d.Zd = f->Zd;
   d.T = f->T; d.xH2 = f->x_h2; d.xHp = f->x_hp; d.xe = f->x_e; d.xCp = f->x_cp; d.xCO = f->x_co;
   d.nsub = f->nsub; d.status = f->status; d.iters = f->newton_iters;
+  d.hint = f->cost_hint;
   d.ncell = f->ncell;
   d.Zg_val = f->Zg_val; d.Zd_val = f->Zd_val;
   return d;
@@ -325,6 +327,7 @@ int tc_step_host(tc_handle* h, const tc_fields* f, double dt_s, void* stream) {
   d.nsub = f->nsub ? h->d_ibuf : nullptr;
   d.status = f->status ? h->d_ibuf + n : nullptr;
   d.newton_iters = f->newton_iters ? h->d_ibuf + 2 * n : nullptr;
+  d.cost_hint = nullptr;  // a host array here; the predicted order is used
   rc = enqueue(h, false, dev_fields(&d), f->ncell, dt_s, st);
   if (rc != TC_OK) return rc;
   for (int k = 0; k < NST; ++k)

@@ -30,6 +30,7 @@ struct DevFields {
   long long ncell;
   double Zg_val, Zd_val;
   const double* chi0 = nullptr;   // optional per-cell unattenuated FUV scale (driver runs)
+  const int* hint = nullptr;      // optional per-cell cost hint for the cost-ordered queue
 };
 
 // Box table for batched launches: cells [start[b], start[b+1]) belong to box b.

@@ -48,6 +48,16 @@ __global__ void __launch_bounds__(128) k_order_key(DevFields f1, const BoxTable*
     DevFields fb;
     long long li;
     locate<BATCH>(f1, boxes, gi, fb, li);
+    if (fb.hint) {
+      // a caller's cost estimate (e.g. the previous step's Newton iterations): eighth
+      // octaves of 1 + hint
+      const double u = 8.0 * log2(1.0 + fmax((double)fb.hint[li], 0.0));
+      const int bh = (u >= ORDER_BUCKETS - 1) ? ORDER_BUCKETS - 1 : (int)u;
+      const int kh = ORDER_BUCKETS - 1 - bh;
+      key[gi] = (unsigned char)kh;
+      atomicAdd(&sh[kh], 1u);
+      continue;
+    }
     CellC<double> c;
     double T0, x20, xp0;
     load_cell(fb, li, p, c, T0, x20, xp0);

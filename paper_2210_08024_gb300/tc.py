@@ -53,7 +53,7 @@ class tc_fields(ctypes.Structure):
         ("nsub", _P), ("status", _P),
         ("ncell", ctypes.c_longlong),
         ("Zg_val", ctypes.c_double), ("Zd_val", ctypes.c_double),
-        ("newton_iters", _P),
+        ("newton_iters", _P), ("cost_hint", _P),
     ]
 
 
@@ -61,7 +61,7 @@ class tc_fields(ctypes.Structure):
 FIELD_KEYS = {
     "n": "n", "chi_pe": "chi_pe", "chi_lw": "chi_lw", "f_shld_h2": "f_h2", "f_shld_c": "f_c", "F_lyc": "F_lyc",
     "xi_cr": "xi", "Zg": "Zg", "Zd": "Zd", "T": "T", "x_h2": "xH2", "x_hp": "xHp", "x_e": "xe", "x_cp": "xCp",
-    "x_co": "xCO", "nsub": "nsub", "status": "status", "newton_iters": "iters",
+    "x_co": "xCO", "nsub": "nsub", "status": "status", "newton_iters": "iters", "cost_hint": "cost_hint",
 }
 
 

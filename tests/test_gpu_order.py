@@ -59,3 +59,32 @@ def test_order_in_batched_graph(tc):
     for a, b in zip(outs[0], outs[1]):
         for k in KEYS:
             assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_cost_hint_does_not_change_results(tc, mode):
+    # a second step ordered by the first step's Newton iterations, and one ordered by a
+    # meaningless hint, give the results of index order bit for bit
+    import torch
+    c = synthgen.slab(ncell=50000, key=12)
+    d = tc.to_device(c)
+    st = tc.Stepper(mode)
+    st.step(d, DT)
+    torch.cuda.synchronize()
+    start = {k: d[k].clone() for k in ("T", "xH2", "xHp")}
+    hints = {"previous": d["iters"].clone(),
+             "random": torch.randint(0, 1000, (c["n"].size,), dtype=torch.int32, device="cuda")}
+    outs = {}
+    for name in ("none", "previous", "random"):
+        for k in start:
+            d[k].copy_(start[k])
+        d["cost_hint"] = hints.get(name)
+        s2 = tc.Stepper(mode, order_cells=0 if name == "none" else 1)
+        s2.step(d, DT)
+        torch.cuda.synchronize()
+        s2.close()
+        outs[name] = tc.from_device(d)
+    st.close()
+    for name in ("previous", "random"):
+        for k in KEYS:
+            assert np.array_equal(outs["none"][k], outs[name][k]), (name, k)
