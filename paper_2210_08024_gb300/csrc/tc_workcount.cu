@@ -92,7 +92,7 @@ int main(int argc, char** argv) {
   if (fread(a.data(), 8, a.size(), fh) != a.size() || fread(&dt, 8, 1, fh) != 1) return 5;
   fclose(fh);
   auto col = [&](int k) { return a.data() + (size_t)k * n; };
-  DevParams p{1.0, 2.73, 1.0, 1.0, 1.0 / 3.0, 0.1, 1e-3, 1e-12, 1e-7, 1.0, 50, 1000000, 0};
+  DevParams p{1.0, 2.73, 1.0, 1.0, 1.0 / 3.0, 0.1, 1e-3, 1e-12, 1e-6, 1.0, 50, 1000000, 0};  // library defaults
 
   // ---- pass 1: cost per call of each block (FP64), averaged over the sample's cells
   OpCnt c_chem{}, c_cool{}, c_src{}, c_eq_set{}, c_eq_it{}, c_dust_set{}, c_dust_it{};
