@@ -69,7 +69,7 @@ int tc_eq_spec_default(tc_eq_spec *s);
 /* Waits for the work already on `stream`, copies the host arrays of `s` to the device,
  * then enqueues the whole integration (nchunk step launches, each preceded by a small
  * set-up kernel, and two reduction kernels) and returns without waiting for it.  The
- * handle keeps a device workspace of 11 doubles and 2 ints per cell, grown (cudaMalloc)
+ * handle keeps a device workspace of 11 doubles and 3 ints per cell, grown (cudaMalloc)
  * when a call needs more.  TC_EINVAL for a bad spec or output (non-finite or negative
  * values, n_H <= 0, 2 x_H2 + x_H+ > 1), TC_ENOMLP for a seeded mode without weights. */
 int tc_eq_curves(tc_handle *h, const tc_eq_spec *s, const tc_eq_out *o, void *stream);

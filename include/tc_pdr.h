@@ -56,7 +56,7 @@ int tc_pdr_spec_default(tc_pdr_spec *s);
 /* Waits for the work already on `stream`, copies the host arrays of `s`, then enqueues
  * the run (per chunk: a field kernel and a step launch; then the final fields and the
  * transition columns) and returns without waiting for it.  Shares the handle's driver
- * workspace with tc_eq_curves (11 doubles and 2 ints per cell, grown by cudaMalloc).
+ * workspace with tc_eq_curves (11 doubles and 3 ints per cell, grown by cudaMalloc).
  * TC_EINVAL for a bad spec or output, TC_ENOMLP for a seeded mode without weights. */
 int tc_pdr(tc_handle *h, const tc_pdr_spec *s, const tc_pdr_out *o, void *stream);
 

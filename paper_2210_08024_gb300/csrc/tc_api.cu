@@ -458,10 +458,13 @@ extern "C" int tc_sync_status(tc_handle* h, const int* status, long long ncell, 
 }
 
 // ----- driver workspace shared by the one-zone and PDR drivers
-// Grows the per-cell workspace (DRIVER_NW doubles and 2 ints per cell) and the
+// Grows the per-cell workspace (DRIVER_NW doubles and DRIVER_NI ints per cell) and the
 // parameter buffer, waits for earlier work on the stream (it may still read the previous
 // call's parameters), copies the five host parameter arrays and waits for the copies.
 static const size_t DRIVER_NW = 11;
+// ints: the latest launch's status, the OR of the earlier ones, and each cell's Newton
+// iterations in the latest chunk (the cost hint of the next chunk's cell order)
+static const size_t DRIVER_NI = 3;
 
 static int driver_setup(tc_handle* h, size_t ncell, const double* const hp[5], const size_t len[5], double* dp[5],
                         cudaStream_t st) {
@@ -472,7 +475,7 @@ static int driver_setup(tc_handle* h, size_t ncell, const double* const hp[5], c
     h->d_eqi = nullptr;
     h->eq_cells = 0;
     if (cudaMalloc(&h->d_eq, ncell * DRIVER_NW * sizeof(double)) != cudaSuccess) return TC_ENOMEM;
-    if (cudaMalloc(&h->d_eqi, ncell * 2 * sizeof(int)) != cudaSuccess) return TC_ENOMEM;
+    if (cudaMalloc(&h->d_eqi, ncell * DRIVER_NI * sizeof(int)) != cudaSuccess) return TC_ENOMEM;
     h->eq_cells = ncell;
   }
   size_t npar = 0;
@@ -516,7 +519,7 @@ static tcg::DevFields driver_fields(tc_handle* h, size_t n, double* T, double* x
   f.Zg = b + 5 * n; f.Zd = b + 6 * n; f.chi0 = b + 7 * n;
   f.fc = nullptr; f.Flyc = nullptr;
   f.T = T; f.xH2 = xH2; f.xHp = xHp; f.xe = xe; f.xCp = nullptr; f.xCO = xCO;
-  f.nsub = nullptr; f.status = h->d_eqi; f.iters = nullptr;
+  f.nsub = nullptr; f.status = h->d_eqi; f.iters = h->d_eqi + 2 * n;
   f.ncell = (long long)n;
   return f;
 }
@@ -587,6 +590,7 @@ extern "C" int tc_eq_curves(tc_handle* h, const tc_eq_spec* s, const tc_eq_out* 
     if (tcg::launch_eq_fields(g, w, o->T, o->x_h2, o->x_hp, k, k == s->nchunk - 1, st) != cudaSuccess)
       return TC_ECUDA;
     h->launches += 1;
+    f.hint = (k > 0) ? f.iters : nullptr;  // order each chunk by the previous chunk's iterations
     int rc = enqueue(h, false, f, ncell, dt, st);
     if (rc != TC_OK) return rc;
   }
@@ -660,6 +664,7 @@ extern "C" int tc_pdr(tc_handle* h, const tc_pdr_spec* s, const tc_pdr_out* o, v
     if (tcg::launch_pdr_fields(g, w, o->T, o->x_h2, o->x_hp, k, false, nullptr, nullptr, nullptr, st) != cudaSuccess)
       return TC_ECUDA;
     h->launches += 1;
+    f.hint = (k > 0) ? f.iters : nullptr;  // order each chunk by the previous chunk's iterations
     int rc = enqueue(h, false, f, ncell, dt, st);
     if (rc != TC_OK) return rc;
   }
