@@ -45,11 +45,11 @@ FP64_NOMINAL_TFLOPS = 1.25
 STATE_KEYS = ("T", "xH2", "xHp")
 # DRAM bytes per cell of one k_step<1> launch, from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum on a 112^3 slab, profiles/k_step_fp64_slab128.md), scaled by cells:
-# 27.99 GB read + 27.31 GB written for 1,404,928 cells.  Almost all of it is the
+# 24.80 GB read + 22.99 GB written for 1,404,928 cells.  Almost all of it is the
 # per-thread stack (spilled registers and the structs the out-of-line physics calls pass)
 # of 8 resident blocks per SM, ~2 MB of local memory per SM, more than L1 and L2 hold;
 # at the kernel's speed that is ~230 GB/s, 3% of HBM.  The cells' own data are 152 B.
-TRAFFIC_BYTES_PER_CELL = 39361.0
+TRAFFIC_BYTES_PER_CELL = 34016.5
 
 
 def parse():

@@ -257,60 +257,92 @@ TCG_FN bool damped_step(double* y, const double* d, double* st) {
   return full;
 }
 
-// One Newton iteration on y - y^n - dts f(y) = 0: forward-difference Jacobian
-// (relative step 1e-7, abundance steps floored at 1e-17), a damped step, and the test
-// that every full step is below rtol |y_i|.  Returns 1 when converged, 0 to continue,
-// -1 on failure (singular Jacobian or a non-finite state).
+// Jacobian reuse.  Once a full (undamped) Newton step is below JAC_REUSE |y_i| in every
+// component, the next iterations keep that Jacobian (chord iterations: f at the base
+// point only, instead of at four points) for as long as each step is full and at most
+// half the previous one; otherwise the next iteration rebuilds it.  The root and the
+// convergence test are those of the plain iteration: near the root a chord step
+// contracts by about JAC_REUSE times the relative curvature of f, far below the 1/2 that
+// keeps the reuse going.
+constexpr double JAC_REUSE = 1e-3;
+
+// One iteration on y - y^n - dts f(y) = 0.  With `reuse` false: forward-difference
+// Jacobian (relative step 1e-7, abundance steps floored at 1e-17), kept in Jk; with
+// `reuse` true: the Jacobian Jk of an earlier iteration.  Then a damped step and the
+// test that every full step is below rtol |y_i|.  `rel` returns the step's largest
+// relative component and `full` whether no damping limit acted.  Returns 1 when
+// converged, 0 to continue, -1 on failure (singular Jacobian or a non-finite state).
 TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
-                       double dts, double* y, double& xe_g, double& td_g) {
-  TCG_COUNT_D(newton64_it);
+                       double dts, double* y, double& xe_g, double& td_g, double (*Jk)[3], bool reuse,
+                       double& rel, bool& full) {
   double f0[3], J[3][3];
   ChemT<double> b = chem_T(c, mu * y[0], p.flags);
   CoolT<double> k = cool_T(c, b, p.flags);
-  // evaluation order: x_H2 column, x_H+ column, base point (all at the base T), then
-  // the T_mu column, so the temperature blocks are built twice per iteration.
-  double fx[2][3];
+  if (reuse) {
+    TCG_COUNT_D(chord64_it);
+    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) J[i][j] = Jk[i][j];
+  } else {
+    TCG_COUNT_D(newton64_it);
+    // evaluation order: x_H2 column, x_H+ column, base point (all at the base T), then
+    // the T_mu column, so the temperature blocks are built twice per iteration.
+    double fx[2][3];
 #pragma unroll 1
-  for (int j = 1; j < 3; ++j) {
-    double h = fmax(1e-7 * fabs(y[j]), 1e-17);
-    double y1 = y[1] + ((j == 1) ? h : 0.0), y2 = y[2] + ((j == 2) ? h : 0.0);
-    double xg = xe_g, tg = td_g;
-    feval64(c, b, k, y1, y2, Kinv, xg, tg, fx[j - 1]);
-  }
-  feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0);
-  for (int j = 1; j < 3; ++j) {
-    double h = fmax(1e-7 * fabs(y[j]), 1e-17);
-    for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - dts * (fx[j - 1][i] - f0[i]) / h;
-  }
-  {
-    double h = 1e-7 * y[0];
-    ChemT<double> bT = chem_T(c, mu * (y[0] + h), p.flags);
-    CoolT<double> kT = cool_T(c, bT, p.flags);
-    double xg = xe_g, tg = td_g;
-    double fT[3];
-    feval64(c, bT, kT, y[1], y[2], Kinv, xg, tg, fT);
-    for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - dts * (fT[i] - f0[i]) / h;
+    for (int j = 1; j < 3; ++j) {
+      double h = fmax(1e-7 * fabs(y[j]), 1e-17);
+      double y1 = y[1] + ((j == 1) ? h : 0.0), y2 = y[2] + ((j == 2) ? h : 0.0);
+      double xg = xe_g, tg = td_g;
+      feval64(c, b, k, y1, y2, Kinv, xg, tg, fx[j - 1]);
+    }
+    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0);
+    for (int j = 1; j < 3; ++j) {
+      double h = fmax(1e-7 * fabs(y[j]), 1e-17);
+      for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - dts * (fx[j - 1][i] - f0[i]) / h;
+    }
+    {
+      double h = 1e-7 * y[0];
+      ChemT<double> bT = chem_T(c, mu * (y[0] + h), p.flags);
+      CoolT<double> kT = cool_T(c, bT, p.flags);
+      double xg = xe_g, tg = td_g;
+      double fT[3];
+      feval64(c, bT, kT, y[1], y[2], Kinv, xg, tg, fT);
+      for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - dts * (fT[i] - f0[i]) / h;
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Jk[i][j] = J[i][j];
   }
   double rhs[3], d[3];
   for (int i = 0; i < 3; ++i) rhs[i] = -(y[i] - yn[i] - dts * f0[i]);
   if (!solve3(J, rhs, d)) return -1;
   double st[3];
-  bool conv = damped_step(y, d, st);
-  for (int i = 0; i < 3; ++i)
+  full = damped_step(y, d, st);
+  bool conv = full;
+  rel = 0.0;
+  for (int i = 0; i < 3; ++i) {
     if (fabs(st[i]) > p.rtol * fabs(y[i]) + 1e-300) conv = false;
+    rel = fmax(rel, fabs(st[i]) / (fabs(y[i]) + 1e-300));
+  }
   if (!finite3(y[0], y[1], y[2])) return -1;
   return conv ? 1 : 0;
 }
 
-// One Newton solve from `y` (seed on entry, root on exit).  Returns the iterations
-// used, or -1.
+// One Newton solve from `y` (seed on entry, root on exit), with the Jacobian reuse
+// above.  Returns the iterations used (chord iterations included), or -1.
 TCG_FN int newton_solve(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
                         double dts, double* y, double& xe_g, double& td_g, int maxit = 0) {
   const int nmax = (maxit > 0 && maxit < p.newton_max) ? maxit : p.newton_max;
+  double Jk[3][3];
+  bool reuse = false;
+  double prev = 1.0;
   for (int it = 1; it <= nmax; ++it) {
-    const int r = newton_iter(c, p, mu, Kinv, yn, dts, y, xe_g, td_g);
+    double rel;
+    bool full;
+    const int r = newton_iter(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, Jk, reuse, rel, full);
     if (r < 0) return -1;
     if (r > 0) return it;
+    reuse = full && rel < JAC_REUSE && (!reuse || rel <= 0.5 * prev);
+    prev = rel;
   }
   return -1;
 }
