@@ -22,6 +22,16 @@ cells (hot gas cooling through 1e4 K over many substeps) the two branches end ~1
 apart in T: the oracle itself, given one input abundance one unit in the last place
 away, lands on the other branch.  Tests on such workloads add four times the oracle's
 spread over one-ulp changes of T, x_H2 and x_H+ (``ulp_spread(..., inputs=...)``).
+
+A solver can also change the substep grid by converging where the oracle's FP64 Newton
+does not.  In rare cells the damped FP64 iteration falls into a cycle (T thrown to the
+1% floor and back) and the oracle halves the substep, while the mixed solve (FP32
+Jacobian rebuilt at most twice) converges at full length to a root polished in FP64.
+The two then integrate the same equations on different substep grids, and differ by
+the scheme's time-discretization error, not by rounding.  For cells where exactly one
+side halved a substep (status bit 2), tests may add four times the oracle's own
+grid sensitivity: the change of its result when the substep limiter is halved
+(``grid_spread``).
 """
 import numpy as np
 
@@ -52,6 +62,16 @@ def ulp_spread(oracle_mod, cells, dt, params, inputs=("T",)):
             for k in spread:
                 spread[k] = np.maximum(spread[k], np.abs(r2[k] - base[k]))
     return base, spread
+
+
+def grid_spread(oracle_mod, cells, dt, params, mask):
+    """Per-cell change of the oracle's outputs when its substep limiter is halved (the
+    scheme's time-discretization error on that cell), on the cells of `mask`; zero
+    elsewhere."""
+    base = oracle_mod.step(cells, dt, params)
+    half = oracle_mod.default_params(mode=params.mode, limiter=0.5 * params.limiter, flags=params.flags)
+    r2 = oracle_mod.step(cells, dt, half)
+    return {k: np.where(mask, np.abs(r2[k] - base[k]), 0.0) for k in ("T", "xH2", "xHp")}
 
 
 def assert_fp64_parity(gpu, ref, label="", spread=None):
