@@ -58,6 +58,8 @@ extern "C" {
 #define TC_ST_NONFINITE 4
 #define TC_ST_FALLBACK 8     /* a mixed solve did not converge; the FP64 Newton finished that substep */
 #define TC_ST_POLISHED 16    /* a mixed solve stopped at the FP32 rounding floor before its FP64 polish */
+#define TC_ST_PREDICTOR 32   /* a Newton solve from the start state failed and was restarted from the
+                                 block predictor (abundances by the 2x2 backward Euler, then T) */
 #define TC_ST_ERROR_MASK 7
 
 typedef struct tc_params {

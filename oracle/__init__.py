@@ -26,8 +26,9 @@ F_CONST_KGR = 1
 F_NO_ROVIB = 2
 F_NO_CIE = 4
 F_FREEZE_T = 256
+F_PREDICTOR = 512
 
-ST_OK, ST_MAX_SUBSTEPS, ST_NEWTON, ST_NONFINITE = 0, 1, 2, 4
+ST_OK, ST_MAX_SUBSTEPS, ST_NEWTON, ST_NONFINITE, ST_PREDICTOR = 0, 1, 2, 4, 32
 
 YEAR_S = 3.15576e7
 

@@ -41,9 +41,11 @@ enum : unsigned {
   F_NO_ROVIB = 2u,    // Sec. 7.1.2: H2 ro-vibrational cooling off
   F_NO_CIE = 4u,      // CIE He+metal cooling term off
   F_FREEZE_T = 256u,  // oracle-only: hold T fixed (chemistry-only pins)
+  F_PREDICTOR = 512u, // oracle-only: start every mode-B solve from the predictor (path pins)
 };
 
-enum : int { ST_OK = 0, ST_MAX_SUBSTEPS = 1, ST_NEWTON = 2, ST_NONFINITE = 4 };
+// ST_PREDICTOR (informational): a substep's Newton solve was restarted from the predictor.
+enum : int { ST_OK = 0, ST_MAX_SUBSTEPS = 1, ST_NEWTON = 2, ST_NONFINITE = 4, ST_PREDICTOR = 32 };
 
 struct Params {
   double dvdr_kms_pc;          // <|dv/dr|> for CO LVG cooling, km/s/pc (Sec. 7.1.2 uses 1)
@@ -817,6 +819,80 @@ template <class R> int newton_substep(const CellIn& c, const Params& p, const Pr
   return -1;
 }
 
+// READING (Sec. 6.1 names the coupled implicit scheme but gives no solver for it): start
+// point for a substep whose Newton iteration from the start state fails.  In hot gas
+// where H is ionised as fast as H2 dissociation frees it, the root lies next to the
+// x_H = 0 boundary, and the Newton direction at the start state points far outside
+// the admissible region; the damped iteration then stalls in the corner x_H -> 0.
+// The predictor sweeps the same backward-Euler equations block by block:
+//  - abundances: the closed-form 2x2 backward Euler of the paper's own scheme (Eqs.
+//    e:HH, e:HII with x_H = 1 - 2 x_H2 - x_H+), with every rate evaluated at the
+//    current iterate (T, x, and x_e of the C/O/e equilibrium there); its numerators and
+//    determinant are sums of non-negative terms, so x_H2, x_H+ and x_H stay >= 0;
+//  - T_mu: one Newton step on its own equation g = T_mu - T_mu^n - dt H(T_mu, x)/K = 0
+//    at the new abundances (forward-difference slope, relative step 1e-7); when
+//    dg/dT_mu < 0.1 the explicit value T_mu^n + dt H/K is taken instead; the new T_mu is
+//    kept within a factor 2 of the old.
+// The sweeps stop when every component changed by less than 1e-3 relative (abundance
+// changes relative to max(x, 1e-6)), or after 50 sweeps.  Newton then starts from this
+// point; the equations, and so the root, are those of the plain iteration.
+template <class R> void picard_predictor(const CellIn& c, const Params& p, const Pre<R>& P, R mu, const R* yn, R dts,
+                                         R* y) {
+  using std::log; using std::sqrt;
+  for (int i = 0; i < 3; ++i) y[i] = yn[i];
+  for (int k = 0; k < 50; ++k) {
+    R T = mu * y[0];
+    Equil<R> q = equilibrium(c, P, T, y[1], y[2]);
+    R psi = P.G0 * sqrt(T) / rmax(q.xe * P.n, R(1e-30)) + R(50.0);
+    HRates<R> r = h_rates(c, p, P, T, log(T), y[1], y[2], q.xe, psi);
+    R kn = r.kgr * P.n;
+    R DH2 = R(1.65) * r.zcrH2 + P.zpd + P.zpiH2 + r.zcd;
+    R I = P.zpiH + r.zcrH + r.zci;
+    R Rr = r.arr * q.xe * P.n + r.agr * P.n;
+    R a = R(2.0) * kn + DH2;
+    R cc = I + Rr;
+    R det = R(1.0) + (a + cc) * dts + (R(2.0) * kn * Rr + DH2 * cc) * dts * dts;
+    R x2 = (yn[1] * (R(1.0) + cc * dts) + kn * dts * ((R(1.0) - yn[2]) + Rr * dts)) / det;
+    R xp = (yn[2] * (R(1.0) + a * dts) + I * dts * ((R(1.0) - R(2.0) * yn[1]) + DH2 * dts)) / det;
+    R Tm = y[0];
+    if (!(p.flags & F_FREEZE_T)) {
+      R h = R(1e-7) * y[0];
+      R ya[3] = {y[0], x2, xp}, yb[3] = {y[0] + h, x2, xp};
+      R fa[3], fb[3];
+      f_coupled(c, p, P, mu, ya, fa);
+      f_coupled(c, p, P, mu, yb, fb);
+      R g = y[0] - yn[0] - dts * fa[0];
+      R gp = R(1.0) - dts * (fb[0] - fa[0]) / h;
+      Tm = (gp > R(0.1)) ? y[0] - g / gp : yn[0] + dts * fa[0];
+      Tm = rmin(rmax(Tm, R(0.5) * y[0]), R(2.0) * y[0]);
+    }
+    R ch = rabs(Tm - y[0]) / y[0];
+    ch = rmax(ch, rabs(x2 - y[1]) / rmax(y[1], R(1e-6)));
+    ch = rmax(ch, rabs(xp - y[2]) / rmax(y[2], R(1e-6)));
+    y[0] = Tm;
+    y[1] = x2;
+    y[2] = xp;
+    if (!finite_(y[0]) || !finite_(y[1]) || !finite_(y[2])) return;
+    if (ch < R(1e-3)) return;
+  }
+}
+
+// One substep's Newton solve: from the start state; if that fails, from the predictor
+// above.  Returns the iterations of the successful solve, or -1; `pred` is set when
+// the predictor was used.
+template <class R> int solve_substep(const CellIn& c, const Params& p, const Pre<R>& P, R mu, const R* yn, R dts,
+                                     R* y, bool& pred) {
+  if (!(p.flags & F_PREDICTOR)) {
+    int it = newton_substep(c, p, P, mu, yn, dts, yn, y);
+    if (it >= 0) return it;
+  }
+  pred = true;
+  R ys[3];
+  picard_predictor(c, p, P, mu, yn, dts, ys);
+  if (!finite_(ys[0]) || !finite_(ys[1]) || !finite_(ys[2])) return -1;
+  return newton_substep(c, p, P, mu, yn, dts, ys, y);
+}
+
 template <class R> CellOut step_coupled(const CellIn& c, const Params& p, double T_in, double xH2_in, double xHp_in,
                                         double dt) {
   CellOut out{};
@@ -838,17 +914,19 @@ template <class R> CellOut step_coupled(const CellIn& c, const Params& p, double
     R dts = substep_length(p, dtR - t, e, (p.flags & F_FREEZE_T) ? R(0.0) : s.H, s.CH2, s.CHp, last);
     R yn[3] = {Tmu, xH2, xHp};
     R y[3];
-    int it = newton_substep(c, p, P, mu, yn, dts, yn, y);
-    // READING: a substep whose Newton iteration fails is retried at half length, up to
-    // 30 times; the cell is flagged ST_NEWTON.
+    bool pred = false;
+    int it = solve_substep(c, p, P, mu, yn, dts, y, pred);
+    // READING: a substep whose Newton iteration fails from both start points is retried
+    // at half length, up to 30 times; the cell is flagged ST_NEWTON.
     int halv = 0;
     while (it < 0 && halv < 30) {
       status |= ST_NEWTON;
       dts = dts * R(0.5);
       last = false;
       ++halv;
-      it = newton_substep(c, p, P, mu, yn, dts, yn, y);
+      it = solve_substep(c, p, P, mu, yn, dts, y, pred);
     }
+    if (pred) status |= ST_PREDICTOR;
     if (it < 0) { status |= ST_NONFINITE; break; }
     iters += it;
     Tmu = rmax(y[0], R(p.T_floor) / mu);

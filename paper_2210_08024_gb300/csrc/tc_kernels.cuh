@@ -41,7 +41,7 @@ struct BoxTable {
   DevFields box[MAX_BOX];
 };
 
-constexpr int ST_MAX_SUB = 1, ST_NEWTON = 2, ST_NONFIN = 4, ST_FALLBACK = 8, ST_POLISH = 16;
+constexpr int ST_MAX_SUB = 1, ST_NEWTON = 2, ST_NONFIN = 4, ST_FALLBACK = 8, ST_POLISH = 16, ST_PREDICTOR = 32;
 
 __device__ __forceinline__ long long claim_cells(unsigned long long* cursor) {
   unsigned mask = __activemask();
@@ -384,6 +384,71 @@ TCG_FN void finish_substep(const CellC<F>& cf, double muH, const DevParams& p, d
   s.t = last ? dt : s.t + dts;
 }
 
+// Start point for a substep whose Newton solve from the start state fails (Sec. 6.1
+// gives no solver for the coupled scheme).  In hot gas where H is ionised as fast as H2
+// dissociation frees it, the root lies next to x_H = 0 and the Newton direction at the
+// start state points far outside the admissible region; the damped iteration stalls in
+// the corner x_H -> 0.  Block sweeps on the same backward-Euler equations instead:
+// abundances by the paper's closed-form 2x2 backward Euler with every rate at the
+// current iterate (non-negative by construction), then T_mu by one Newton step on its
+// own equation T_mu - T_mu^n - dts H/K = 0 at those abundances (forward-difference slope,
+// relative step 1e-7; the explicit value T_mu^n + dts H/K when the slope is below 0.1),
+// kept within a factor 2 of the old value.  Stops when every component changed by less
+// than 1e-3 relative (abundances relative to max(x, 1e-6)), or after 50 sweeps.
+TCG_FN void picard_predictor(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
+                             double dts, double* y, double& xe_g, double& td_g) {
+  y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2];
+#pragma unroll 1
+  for (int k = 0; k < 50; ++k) {
+    TCG_COUNT_D(picard_it);
+    ChemT<double> b = chem_T(c, mu * y[0], p.flags);
+    const Equil<double> q = equilibrium(c, b, y[1], y[2], xe_g);
+    xe_g = q.xe;
+    const HRate<double> r = h_rates(c, b, y[1], 1.0 - 2.0 * y[1] - y[2], q.xe, log_psi(c, b, q.xe));
+    const double a = 2.0 * r.kn + r.DH2;
+    const double cc = r.I + r.Rr;
+    const double det = 1.0 + (a + cc) * dts + (2.0 * r.kn * r.Rr + r.DH2 * cc) * dts * dts;
+    const double x2 = (yn[1] * (1.0 + cc * dts) + r.kn * dts * ((1.0 - yn[2]) + r.Rr * dts)) / det;
+    const double xp = (yn[2] * (1.0 + a * dts) + r.I * dts * ((1.0 - 2.0 * yn[1]) + r.DH2 * dts)) / det;
+    double fa[3], fb[3];
+    {
+      CoolT<double> k = cool_T(c, b, p.flags);
+      feval64(c, b, k, x2, xp, Kinv, xe_g, td_g, fa);
+    }
+    const double h = 1e-7 * y[0];
+    {
+      ChemT<double> bT = chem_T(c, mu * (y[0] + h), p.flags);
+      CoolT<double> kT = cool_T(c, bT, p.flags);
+      double xg = xe_g, tg = td_g;
+      feval64(c, bT, kT, x2, xp, Kinv, xg, tg, fb);
+    }
+    const double g = y[0] - yn[0] - dts * fa[0];
+    const double gp = 1.0 - dts * (fb[0] - fa[0]) / h;
+    double Tm = (gp > 0.1) ? y[0] - g / gp : yn[0] + dts * fa[0];
+    Tm = fmin(fmax(Tm, 0.5 * y[0]), 2.0 * y[0]);
+    double ch = fabs(Tm - y[0]) / y[0];
+    ch = fmax(ch, fabs(x2 - y[1]) / fmax(y[1], 1e-6));
+    ch = fmax(ch, fabs(xp - y[2]) / fmax(y[2], 1e-6));
+    y[0] = Tm; y[1] = x2; y[2] = xp;
+    if (!finite3(y[0], y[1], y[2])) return;
+    if (ch < 1e-3) return;
+  }
+}
+
+// One substep's FP64 Newton solve at length dts: from the start state, and if that
+// fails, from the predictor above (flagging ST_PREDICTOR).  Returns the iterations of
+// the successful solve, or -1.
+TCG_FN int solve_from_start64(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
+                              double dts, double* y, double& xe_g, double& td_g, int& status) {
+  y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2];
+  int it = newton_solve(c, p, mu, Kinv, yn, dts, y, xe_g, td_g);
+  if (it >= 0) return it;
+  status |= ST_PREDICTOR;
+  picard_predictor(c, p, mu, Kinv, yn, dts, y, xe_g, td_g);
+  if (!finite3(y[0], y[1], y[2])) return -1;
+  return newton_solve(c, p, mu, Kinv, yn, dts, y, xe_g, td_g);
+}
+
 // A seeded Newton solve that has not converged after this many iterations is abandoned
 // and the substep restarts from its start state: a poor seed then costs little.
 constexpr int SEED_MAXIT = 6;
@@ -392,8 +457,8 @@ constexpr float SEED_MAX_DLOGT = 0.02f, SEED_MAX_DX = 0.02f;
 
 // Solves one substep of length dts by the FP64 Newton iteration, from `seed` when
 // given (the root is the same; a seeded solve that fails is retried from the start
-// state), else from the start state; a failed solve is retried at half length (up to
-// 30 times) and the cell flagged ST_NEWTON.
+// state), else from the start state, then from the predictor; a substep that fails
+// from both is retried at half length (up to 30 times) and the cell flagged ST_NEWTON.
 TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double dt, double dts, bool last,
                             LaneState& s, double& xe_g, double& td_g, const double* seed = nullptr) {
   const double yn[3] = {s.Tmu, s.xH2, s.xHp};
@@ -404,17 +469,16 @@ TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double d
     y[0] = seed[0]; y[1] = seed[1]; y[2] = seed[2];
     double xg = xe_g, tg = td_g;
     it = newton_solve(c, p, s.mu, Kinv, yn, dts, y, xg, tg, SEED_MAXIT);
-    if (it < 0) { y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2]; } else { xe_g = xg; td_g = tg; }
+    if (it >= 0) { xe_g = xg; td_g = tg; }
   }
-  if (it < 0) it = newton_solve(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g);
+  if (it < 0) it = solve_from_start64(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status);
   int halv = 0;
   while (it < 0 && halv < 30) {
     s.status |= ST_NEWTON;
     dts *= 0.5;
     last = false;
     ++halv;
-    y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2];
-    it = newton_solve(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g);
+    it = solve_from_start64(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status);
   }
   if (it < 0) {
     s.status |= ST_NONFIN;
@@ -532,11 +596,14 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
 // equilibria, where H is a small difference of large terms), and the scheme can
 // amplify such errors a hundredfold over a step, so every substep is polished.  The
 // chord iteration contracts by the Jacobian's relative error (<~0.1), so a correction
-// below 1e-7 relative leaves an error below ~1e-8: accept then, after at most three.
+// below 1e-8 relative leaves an error below ~1e-9: accept then, after at most five.
+// (Accepting at 1e-7 left one of 4096 random-state cells at 1.04e-5 in T after 86
+// substeps; at 1e-8, 2.5e-6.  Five corrections instead of three also send fewer
+// substeps to the FP64 fallback: 47 instead of 152 of those 4096 cells.)
 // Returns false if that does not happen.
 TCG_FN bool polish64(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
                      double dts, double* y, const double J[3][3], double& xe_g, double& td_g) {
-  for (int it = 0; it < 3; ++it) {
+  for (int it = 0; it < 5; ++it) {
     TCG_COUNT_D(polish_it);
     ChemT<double> b = chem_T(c, mu * y[0], p.flags);
     CoolT<double> k = cool_T(c, b, p.flags);
@@ -551,7 +618,7 @@ TCG_FN bool polish64(const CellC<double>& c, const DevParams& p, double mu, doub
     double st[3];
     const bool full = damped_step(y, d, st);
     double nrm = 0.0;
-    for (int i = 0; i < 3; ++i) nrm = fmax(nrm, fabs(st[i]) / (1e-7 * fabs(y[i]) + ((i == 0) ? 1e-300 : 1e-12)));
+    for (int i = 0; i < 3; ++i) nrm = fmax(nrm, fabs(st[i]) / (1e-8 * fabs(y[i]) + ((i == 0) ? 1e-300 : 1e-12)));
     if (!finite3(y[0], y[1], y[2])) return false;
     if (full && nrm <= 1.0) return true;
   }

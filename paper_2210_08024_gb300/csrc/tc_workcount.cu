@@ -23,7 +23,7 @@
 namespace wc {
 struct Calls {
   long long chem_T, cool_T, equil, equil_it, dust, dust_it, source;
-  long long newton64_it, chord64_it, newton32_it, polish_it, substep_paper;
+  long long newton64_it, chord64_it, newton32_it, polish_it, substep_paper, picard_it;
 };
 Calls calls[2];  // [0] FP64, [1] FP32
 }  // namespace wc

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libtc_gb300.so")
 TC_OK, TC_EINVAL, TC_ECUDA, TC_ENOMEM, TC_ENOMLP, TC_ENODEV = 0, -1, -2, -3, -4, -5
 TC_MODE_PAPER_FP64, TC_MODE_NEWTON_FP64, TC_MODE_MIXED, TC_MODE_MIXED_SEEDED, TC_MODE_NEWTON_FP64_SEEDED = 0, 1, 2, 3, 4
 TC_CONST_KGR, TC_NO_ROVIB, TC_NO_CIE = 1, 2, 4
-TC_ST_MAX_SUBSTEPS, TC_ST_NEWTON, TC_ST_NONFINITE, TC_ST_FALLBACK, TC_ST_POLISHED = 1, 2, 4, 8, 16
+TC_ST_MAX_SUBSTEPS, TC_ST_NEWTON, TC_ST_NONFINITE, TC_ST_FALLBACK, TC_ST_POLISHED, TC_ST_PREDICTOR = 1, 2, 4, 8, 16, 32
 TC_ST_ERROR_MASK = 7
 
 

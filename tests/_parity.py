@@ -16,22 +16,11 @@ to ~1e-9.  The mode-0 bound therefore adds four times that measured one-ulp spre
 
 Mixed path vs the FP64 oracle: 1e-5 relative on T and 1e-6 absolute on abundances.
 
-The coupled scheme (mode 1) halves a substep whose Newton solve fails.  Whether the
-solve of a given substep fails can hinge on the last bit of the state, and in rare
-cells (hot gas cooling through 1e4 K over many substeps) the two branches end ~1e-4
-apart in T: the oracle itself, given one input abundance one unit in the last place
-away, lands on the other branch.  Tests on such workloads add four times the oracle's
-spread over one-ulp changes of T, x_H2 and x_H+ (``ulp_spread(..., inputs=...)``).
-
-A solver can also change the substep grid by converging where the oracle's FP64 Newton
-does not.  In rare cells the damped FP64 iteration falls into a cycle (T thrown to the
-1% floor and back) and the oracle halves the substep, while the mixed solve (FP32
-Jacobian rebuilt at most twice) converges at full length to a root polished in FP64.
-The two then integrate the same equations on different substep grids, and differ by
-the scheme's time-discretization error, not by rounding.  For cells where exactly one
-side halved a substep (status bit 2), tests may add four times the oracle's own
-grid sensitivity: the change of its result when the substep limiter is halved
-(``grid_spread``).
+The coupled scheme (mode 1) carries no such allowance: its result is the backward-Euler
+root of each substep, which does not depend on the path the Newton iteration takes to
+it, and no substep of the test workloads is halved (a solve that fails from the start
+state restarts from the block predictor first), so every FP64 and mixed comparison of
+mode 1 uses the plain bounds above.
 """
 import numpy as np
 
@@ -51,7 +40,7 @@ def rel_err(a, b, floor=0.0):
 def ulp_spread(oracle_mod, cells, dt, params, inputs=("T",)):
     """Largest change of the oracle's outputs when one input state variable (each of
     `inputs` in turn) moves by one unit in the last place (up or down): a per-cell
-    measure of how much rounding the scheme amplifies."""
+    measure of how much rounding the paper's sequential scheme amplifies."""
     base = oracle_mod.step(cells, dt, params)
     spread = {k: np.zeros_like(base[k]) for k in ("T", "xH2", "xHp")}
     for key in inputs:
@@ -62,16 +51,6 @@ def ulp_spread(oracle_mod, cells, dt, params, inputs=("T",)):
             for k in spread:
                 spread[k] = np.maximum(spread[k], np.abs(r2[k] - base[k]))
     return base, spread
-
-
-def grid_spread(oracle_mod, cells, dt, params, mask):
-    """Per-cell change of the oracle's outputs when its substep limiter is halved (the
-    scheme's time-discretization error on that cell), on the cells of `mask`; zero
-    elsewhere."""
-    base = oracle_mod.step(cells, dt, params)
-    half = oracle_mod.default_params(mode=params.mode, limiter=0.5 * params.limiter, flags=params.flags)
-    r2 = oracle_mod.step(cells, dt, half)
-    return {k: np.where(mask, np.abs(r2[k] - base[k]), 0.0) for k in ("T", "xH2", "xHp")}
 
 
 def assert_fp64_parity(gpu, ref, label="", spread=None):
@@ -89,14 +68,11 @@ def assert_fp64_parity(gpu, ref, label="", spread=None):
             label, k, bad.size, np.nanmax(err / np.maximum(np.abs(b), 1e-300)), bad[0], a[bad[0]], b[bad[0]])
 
 
-def assert_mixed_parity(gpu, ref, label="", spread=None):
+def assert_mixed_parity(gpu, ref, label=""):
     b = np.asarray(ref["T"], dtype=np.float64)
     err = np.abs(np.asarray(gpu["T"], dtype=np.float64) - b)
     tol = RTOL_T_MIXED * np.abs(b)
-    if spread is not None:
-        tol = tol + SPREAD_FACTOR * spread["T"]
     assert np.all(err <= tol), "%s T: max rel %.3e" % (label, np.nanmax(err / np.abs(b)))
     for k in ("xH2", "xHp"):
         ea = np.abs(np.asarray(gpu[k]) - np.asarray(ref[k]))
-        tk = ATOL_X_MIXED + (SPREAD_FACTOR * spread[k] if spread is not None else 0.0)
-        assert np.all(ea <= tk), "%s %s: max abs %.3e" % (label, k, np.nanmax(ea))
+        assert np.all(ea <= ATOL_X_MIXED), "%s %s: max abs %.3e" % (label, k, np.nanmax(ea))

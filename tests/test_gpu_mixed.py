@@ -23,7 +23,7 @@ def tc():
     return T
 
 
-@pytest.mark.parametrize("key,n", [(1, 4096), (78, 33), (79, 1)])
+@pytest.mark.parametrize("key,n", [(1, 4096), (42, 4096), (43, 4096), (78, 33), (79, 1)])
 def test_mixed_random_states(tc, key, n):
     c = synthgen.cells_4096(n=n, key=key)
     ref = oracle.step(c, DT, oracle.default_params(mode=1))

@@ -10,7 +10,7 @@ import pytest
 import oracle
 import synthgen
 from oracle import mlp as ref_mlp
-from tests._parity import assert_fp64_parity, assert_mixed_parity, ulp_spread
+from tests._parity import assert_fp64_parity, assert_mixed_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -161,11 +161,12 @@ def test_seeded_fp64_same_root_and_iteration_count(tc, trained_blob, workload):
 
 
 def test_seeded_mixed_within_tolerance(tc, trained_blob):
-    # Random states include hot gas that cools through 1e4 K over ~100 substeps, where
-    # a halved substep makes the result depend on the last bit of the state: the bound
-    # adds the oracle's own one-ulp spread (tests/_parity.py).
+    # Random states include hot molecular gas that cools through 1e4 K over ~100
+    # substeps; no substep of this workload is halved by either side, so the bound is
+    # the plain mixed one, cell by cell.
     c = synthgen.cells_4096(n=4096, key=42)
-    ref, spread = ulp_spread(oracle, c, DT, oracle.default_params(mode=1), inputs=("T", "xH2", "xHp"))
+    ref = oracle.step(c, DT, oracle.default_params(mode=1))
+    assert np.all((ref["status"] & tc.TC_ST_ERROR_MASK) == 0)
     g = _run(tc, c, tc.TC_MODE_MIXED_SEEDED, trained_blob)
-    assert np.all((g["status"] & (tc.TC_ST_NONFINITE | tc.TC_ST_MAX_SUBSTEPS)) == 0)
-    assert_mixed_parity(g, ref, "mixed-seeded", spread=spread)
+    assert np.all((g["status"] & tc.TC_ST_ERROR_MASK) == 0)
+    assert_mixed_parity(g, ref, "mixed-seeded")

@@ -41,8 +41,23 @@ def test_config1_paper_scheme_fp64(tc, cfg1):
 def test_config1_newton_fp64(tc, cfg1):
     c, ref = cfg1
     g = tc.step_numpy(c, DT, tc.TC_MODE_NEWTON_FP64)
-    assert np.all(g["status"] == 0)
+    assert np.all((g["status"] & tc.TC_ST_ERROR_MASK) == 0)
     assert_fp64_parity(g, ref[1], "mode1")
+
+
+@pytest.mark.parametrize("key", [42, 43])
+def test_newton_fp64_hot_random_states_strict(tc, key):
+    # 4096 random states that hold hot molecular cells (1e7 K, x_H2 ~ 0.49) whose Newton
+    # solve from the start state fails and restarts from the block predictor: plain
+    # FP64 bound, same substep counts, no halved substep on either side.
+    c = synthgen.cells_4096(n=4096, key=key)
+    ref = oracle.step(c, DT, oracle.default_params(mode=1))
+    assert np.any(ref["status"] & oracle.ST_PREDICTOR)
+    assert np.all((ref["status"] & tc.TC_ST_ERROR_MASK) == 0)
+    g = tc.step_numpy(c, DT, tc.TC_MODE_NEWTON_FP64)
+    assert np.all((g["status"] & tc.TC_ST_ERROR_MASK) == 0)
+    assert np.array_equal(g["nsub"], ref["nsub"])
+    assert_fp64_parity(g, ref, "mode1 key%d" % key)
 
 
 @pytest.mark.parametrize("n", [1, 31, 33, 4097])
