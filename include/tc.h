@@ -133,7 +133,12 @@ int tc_step(tc_handle *h, const tc_fields *f, double dt_s, void *stream);
 /* Enqueues one step for nbox independent boxes (each its own tc_fields, Z scalars and
  * size) as a single persistent-kernel launch over a device box table; on the first call
  * with a given box set the launch is captured into a CUDA graph that later identical
- * calls replay.  `boxes` is a host array of nbox descriptors. */
+ * calls (same descriptors, dt_s, parameters and stream, compared in full) replay
+ * without blocking.  A call with a different box set first waits on the host for the
+ * cached graph's last launch to finish, since the box table's pinned host copy and
+ * device copy are reused, then captures anew.  `boxes` is a host array of nbox
+ * descriptors (1 <= nbox <= 64), read before the call returns.  Returns TC_EINVAL for a
+ * bad count or descriptor, TC_ECUDA if capture or launch fails. */
 int tc_step_batch(tc_handle *h, const tc_fields *boxes, int nbox, double dt_s, void *stream);
 
 /* Like tc_step but every pointer in *f is a HOST pointer: the call copies inputs to the

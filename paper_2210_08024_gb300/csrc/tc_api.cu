@@ -40,10 +40,16 @@ struct tc_handle {
   double* d_buf = nullptr;
   size_t d_buf_cells = 0;
   int* d_ibuf = nullptr;
-  // batched graph cache
+  // batched graph cache: the executable graph, what it was captured for (box table,
+  // dt, parameters, stream; compared in full, not by a hash), and an event recorded
+  // after each of its launches (the pinned h_boxes and d_boxes are reused only after
+  // the last launch has finished with them)
   cudaGraphExec_t gexec = nullptr;
-  unsigned long long gkey = 0;
+  tcg::BoxTable gtb;
+  double gdt = 0.0;
+  tc_params gp;
   cudaStream_t gstream = nullptr;
+  cudaEvent_t gdone = nullptr;
   // MLP seed weights (device) -- loaded by tc_load_mlp
   void* d_mlp = nullptr;
   size_t mlp_bytes = 0;
@@ -123,6 +129,10 @@ int tc_create(const tc_params* p, tc_handle** out) {
 
 void tc_destroy(tc_handle* h) {
   if (!h) return;
+  if (h->gdone) {
+    cudaEventSynchronize(h->gdone);
+    cudaEventDestroy(h->gdone);
+  }
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   cudaFree(h->d_cursor);
   cudaFree(h->d_boxes);
@@ -344,15 +354,6 @@ int tc_step_host(tc_handle* h, const tc_fields* f, double dt_s, void* stream) {
   return TC_OK;
 }
 
-static unsigned long long fnv1a(const void* data, size_t n, unsigned long long hsh) {
-  const unsigned char* c = (const unsigned char*)data;
-  for (size_t i = 0; i < n; ++i) {
-    hsh ^= c[i];
-    hsh *= 1099511628211ull;
-  }
-  return hsh;
-}
-
 int tc_step_batch(tc_handle* h, const tc_fields* boxes, int nbox, double dt_s, void* stream) {
   if (!h || !boxes || nbox < 1 || nbox > tcg::MAX_BOX) return TC_EINVAL;
   if (!(dt_s >= 0.0) || !isfinite(dt_s)) return TC_EINVAL;
@@ -374,11 +375,12 @@ int tc_step_batch(tc_handle* h, const tc_fields* boxes, int nbox, double dt_s, v
   }
   tb.start[nbox] = tot;
   if (tot == 0) return TC_OK;
-  unsigned long long key = fnv1a(&tb, sizeof(tb), 1469598103934665603ull);
-  key = fnv1a(&dt_s, sizeof(dt_s), key);
-  key = fnv1a(&h->p, sizeof(h->p), key);
-  key = fnv1a(&st, sizeof(st), key);
-  if (!h->gexec || key != h->gkey) {
+  const bool same = h->gexec && memcmp(&tb, &h->gtb, sizeof(tb)) == 0 && memcmp(&dt_s, &h->gdt, sizeof(dt_s)) == 0 &&
+                    memcmp(&h->p, &h->gp, sizeof(h->p)) == 0 && st == h->gstream;
+  if (!same) {
+    // The previous graph's launch may still be in flight, reading h_boxes (its memcpy
+    // node) and d_boxes (its kernel): wait for it before either is rewritten.
+    if (h->gdone && cudaEventSynchronize(h->gdone) != cudaSuccess) return TC_ECUDA;
     if (h->gexec) {
       cudaGraphExecDestroy(h->gexec);
       h->gexec = nullptr;
@@ -406,9 +408,14 @@ int tc_step_batch(tc_handle* h, const tc_fields* boxes, int nbox, double dt_s, v
     e = cudaGraphInstantiate(&h->gexec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return TC_ECUDA;
-    h->gkey = key;
+    memcpy(&h->gtb, &tb, sizeof(tb));
+    memcpy(&h->gdt, &dt_s, sizeof(dt_s));
+    memcpy(&h->gp, &h->p, sizeof(h->p));
+    h->gstream = st;
   }
+  if (!h->gdone && cudaEventCreateWithFlags(&h->gdone, cudaEventDisableTiming) != cudaSuccess) return TC_ECUDA;
   if (cudaGraphLaunch(h->gexec, st) != cudaSuccess) return TC_ECUDA;
+  if (cudaEventRecord(h->gdone, st) != cudaSuccess) return TC_ECUDA;
   h->launches += 1;
   return TC_OK;
 }

@@ -1,6 +1,7 @@
 // Host program that runs the library's own step functions on the CPU, for tests that
 // need no GPU (not part of libtc_gb300.so, and not reachable from the C ABI or the
-// binding; built and run by tests/test_host_step.py).  Each cell goes through the same
+// binding; built and run by tests/test_host_step.py with the library's csrc/ on the
+// include path).  Each cell goes through the same
 // sequence as one lane of k_step: load_cell, the initial C/O/e equilibrium that sets mu,
 // substeps of the selected mode until the step's end (or the substep cap), store_cell.
 // Only host code is executed: the device translation of this file is never launched.

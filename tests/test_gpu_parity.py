@@ -109,6 +109,34 @@ def test_host_buffer_entry_matches_device(tc, cfg1):
     st.close()
 
 
+def test_batched_alternating_box_sets_without_sync(tc):
+    # Two box sets launched in turn, twice each, with no synchronisation between calls:
+    # every call re-captures the batched graph while the previous one may still run, so
+    # each launch must still read its own box table.  Both sets end two steps on.
+    import torch
+    sets = [[synthgen.cells_4096(n=n, key=400 + 10 * s + i, Z=z) for i, (n, z) in enumerate(shape)]
+            for s, shape in enumerate([[(700, 0.5), (300, 2.0)], [(999, 1.0), (64, 0.2), (257, 3.0)]])]
+    st = tc.Stepper(tc.TC_MODE_NEWTON_FP64)
+    devs = [[tc.to_device(b) for b in bs] for bs in sets]
+    for ds in devs:
+        for d in ds:
+            d.pop("Zg"); d.pop("Zd")
+    fields = [[tc.make_fields(d, Zg=float(b["Zg"][0]), Zd=float(b["Zd"][0])) for d, b in zip(ds, bs)]
+              for ds, bs in zip(devs, sets)]
+    for _ in range(2):
+        tc.tc_step_batch(st.h, fields[0], DT)
+        tc.tc_step_batch(st.h, fields[1], DT)
+    torch.cuda.synchronize()
+    p1 = oracle.default_params(mode=1)
+    for ds, bs in zip(devs, sets):
+        for d, b in zip(ds, bs):
+            r1 = oracle.step(b, DT, p1)
+            b2 = dict(b, T=r1["T"], xH2=r1["xH2"], xHp=r1["xHp"])
+            ref = oracle.step(b2, DT, p1)
+            assert_fp64_parity({k: d[k].cpu().numpy() for k in ("T", "xH2", "xHp")}, ref, "alternating")
+    st.close()
+
+
 def test_batched_boxes_match_oracle_and_replay(tc):
     import torch
     boxes = [synthgen.cells_4096(n=n, key=300 + i, Z=z) for i, (n, z) in enumerate([(512, 0.3), (1000, 1.0), (77, 2.5)])]

@@ -1,6 +1,6 @@
 """The library's step functions compiled for the host against the oracle, without a GPU.
 
-csrc/tc_hoststep.cu runs the device code's own substep functions (the paper's scheme,
+tests/host/tc_hoststep.cu runs the device code's own substep functions (the paper's scheme,
 coupled FP64 Newton with its Jacobian reuse, and the mixed FP32/FP64 solve) on the CPU,
 cell by cell as one lane of the step kernel does, with the library's default
 parameters read through the C ABI.  It is a test program outside libtc_gb300.so: a
@@ -30,8 +30,8 @@ def exe(tmp_path_factory):
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
     out = str(tmp_path_factory.mktemp("hoststep") / "tc_hoststep")
-    subprocess.run([nvcc, "-std=c++17", "-O2", "-x", "cu", "-gencode", "arch=compute_103a,code=sm_103a",
-                    os.path.join(CSRC, "tc_hoststep.cu"), "-o", out], check=True, capture_output=True)
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-x", "cu", "-gencode", "arch=compute_103a,code=sm_103a", "-I", CSRC,
+                    os.path.join(ROOT, "tests", "host", "tc_hoststep.cu"), "-o", out], check=True, capture_output=True)
     return out
 
 

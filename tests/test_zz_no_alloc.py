@@ -4,12 +4,15 @@ memory (no handle, no cudaMalloc; device staging in the library's static scratch
 Its results must match the handle-based host entry point tc_step_host at the FP64
 parity tolerance, on two calls in a row.  The second call is smaller and uses other
 inputs, so anything stale that the first call left in the shared scratch, such as the
-work-queue cursor, would show.  The file is named to be collected last."""
+work-queue cursor, would show.  Every mode it accepts (the paper's scheme, the coupled
+FP64 Newton and the mixed solve) is also checked against the CPU oracle.  The file is
+named to be collected last."""
 import numpy as np
 import pytest
 
+import oracle
 import synthgen
-from tests._parity import assert_fp64_parity
+from tests._parity import assert_fp64_parity, assert_mixed_parity, ulp_spread
 
 pytestmark = pytest.mark.gpu
 
@@ -51,6 +54,26 @@ def test_static_entry_matches_host_entry_twice(tc):
             np.testing.assert_allclose(a[k], b[k], rtol=1e-9, atol=1e-14)
         assert np.array_equal(a["nsub"], b["nsub"]) and np.array_equal(a["status"], b["status"])
     st.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_static_entry_matches_oracle_in_every_mode(tc, mode):
+    params = tc.tc_params_default(mode)
+    for n, key in ((2000, 511), (700, 512)):
+        cells = synthgen.cells_4096(n=n, key=key)
+        a = _host_arrays(tc, cells)
+        tc.tc_step_host_static(params, tc.make_host_fields(a), DT)
+        if mode == 0:
+            ref, spread = ulp_spread(oracle, cells, DT, oracle.default_params(mode=0))
+            assert_fp64_parity(a, ref, "static mode0 n=%d" % n, spread=spread)
+        else:
+            ref = oracle.step(cells, DT, oracle.default_params(mode=1))
+            assert np.all((a["status"] & tc.TC_ST_ERROR_MASK) == 0)
+            if mode == 1:
+                assert_fp64_parity(a, ref, "static mode1 n=%d" % n)
+                assert np.array_equal(a["nsub"], ref["nsub"])
+            else:
+                assert_mixed_parity(a, ref, "static mixed n=%d" % n)
 
 
 def test_static_entry_rejects_more_cells_than_its_scratch(tc):
