@@ -191,3 +191,54 @@ def test_unshielded_equilibrium_curve_shape():
     assert a["T_min"] / 1.5 < r["T"][imin] < a["T_min"] * 1.5
     T2e3 = np.interp(np.log(2e3), np.log(n), r["T"])
     assert T2e3 == pytest.approx(a["T_at_2e3"], rel=0.2)
+
+
+def _stiff_class(kind, m, seed):
+    g = np.random.default_rng(seed)
+    if kind == "hot":          # collisionally ionised gas cooling from 1e5-1e7 K
+        c = dict(n=10 ** g.uniform(-2, 1, m), T=10 ** g.uniform(5, 7, m), xH2=np.zeros(m),
+                 xHp=g.uniform(0.5, 1.0, m), chi_pe=10 ** g.uniform(-1, 1, m), f_h2=np.ones(m), F_lyc=np.zeros(m))
+    elif kind == "ionised":    # photoionised gas, F_LyC = 1e7-1e10 cm^-2 s^-1
+        c = dict(n=10 ** g.uniform(0, 2, m), T=10 ** g.uniform(3.7, 4.2, m), xH2=np.zeros(m),
+                 xHp=g.uniform(0.01, 0.99, m), chi_pe=10 ** g.uniform(0, 2, m), f_h2=np.ones(m),
+                 F_lyc=10 ** g.uniform(7, 10, m))
+    else:                      # dense shielded molecular gas
+        c = dict(n=10 ** g.uniform(2, 4, m), T=10 ** g.uniform(1, 2.3, m), xH2=g.uniform(0.3, 0.5, m),
+                 xHp=10 ** g.uniform(-7, -4, m), chi_pe=10 ** g.uniform(-3, -1, m), f_h2=10 ** g.uniform(-6, -2, m),
+                 F_lyc=np.zeros(m))
+    c.update(f_c=1.0, xi=2e-16, Zg=1.0, Zd=1.0)
+    c["chi_lw"] = c["chi_pe"]
+    return c
+
+
+@pytest.mark.parametrize("kind", ["hot", "ionised", "molecular"])
+def test_rk45_convergence_stiff_classes(kind):
+    # 100 cells per class (hot 1e5-1e7 K, photoionised, dense molecular), one step of
+    # dt = 1e4 yr: both schemes approach the tight RK45 solution of the same
+    # differential-algebraic system at first order as the limiter shrinks
+    # 0.01 -> 0.001 -> 0.0001.  The order is taken on the summed error over the cells
+    # (and on the median cell): a few cold cells are still pre-asymptotic at 1e-3.
+    from concurrent.futures import ThreadPoolExecutor
+    m = 100
+    c = _stiff_class(kind, m, 5)
+    dt = 1e4 * YR
+
+    def one(i):
+        cell = {k: (c[k][i] if np.ndim(c[k]) else c[k]) for k in oracle.CELL_KEYS}
+        return oracle.rk45(cell, c["T"][i], c["xH2"][i], c["xHp"][i], dt)[0]
+
+    with ThreadPoolExecutor(8) as ex:
+        ref = np.array(list(ex.map(one, range(m))))
+    for mode in (0, 1):
+        errs = []
+        for lim in (0.01, 0.001, 0.0001):
+            r = oracle.step(c, dt, oracle.default_params(mode=mode, limiter=lim))
+            assert np.all((r["status"] & (oracle.ST_NEWTON | oracle.ST_NONFINITE)) == 0)
+            errs.append(np.abs(r["T"] - ref[:, 0]) / ref[:, 0] + np.abs(r["xH2"] - ref[:, 1]) +
+                        np.abs(r["xHp"] - ref[:, 2]))
+        errs = np.array(errs)
+        l1 = errs.sum(axis=1)
+        assert errs[2].max() < 2e-3, (kind, mode, errs.max(axis=1))
+        for a, b in ((0, 1), (1, 2)):
+            assert 0.85 < math.log10(l1[a] / l1[b]) < 1.15, (kind, mode, l1)
+        assert 0.85 < np.median(np.log10(errs[1] / errs[2])) < 1.15, (kind, mode)
