@@ -165,9 +165,12 @@ TCG_FN void substep_paper(const CellC<double>& c, const DevParams& p, double dt,
 
 // ------------------------------------------------------------------ mode 1: coupled Newton, FP64
 // f(y) = (H/K, C_H2, C_H+) at T = mu^n y0 with the C/O/e equilibrium and T_d re-solved.
+// `qout`, when given, receives the C/O/e equilibrium of the evaluation.
 TCG_FN void feval64(const CellC<double>& c, const ChemT<double>& b, const CoolT<double>& k, double y1,
-                    double y2, double Kinv, double& xe_guess, double& td_guess, double* f) {
+                    double y2, double Kinv, double& xe_guess, double& td_guess, double* f,
+                    Equil<double>* qout = nullptr) {
   Equil<double> q = equilibrium(c, b, y1, y2, xe_guess);
+  if (qout) *qout = q;
   Src<double> s = source(c, b, k, y1, y2, 1.0 - 2.0 * y1 - y2, q, -1.0, td_guess);
   xe_guess = q.xe;
   td_guess = s.Td;
@@ -274,13 +277,13 @@ constexpr double JAC_REUSE = 1e-3;
 // converged, 0 to continue, -1 on failure (singular Jacobian or a non-finite state).
 TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
                        double dts, double* y, double& xe_g, double& td_g, double (*Jk)[3], bool reuse,
-                       double& rel, bool& full) {
+                       double& rel, bool& full, Equil<double>* qb) {
   double f0[3], J[3][3];
   ChemT<double> b = chem_T(c, mu * y[0], p.flags);
   CoolT<double> k = cool_T(c, b, p.flags);
   if (reuse) {
     TCG_COUNT_D(chord64_it);
-    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0);
+    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, qb);
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) J[i][j] = Jk[i][j];
   } else {
@@ -295,7 +298,7 @@ TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, do
       double xg = xe_g, tg = td_g;
       feval64(c, b, k, y1, y2, Kinv, xg, tg, fx[j - 1]);
     }
-    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0);
+    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, qb);
     for (int j = 1; j < 3; ++j) {
       double h = fmax(1e-7 * fabs(y[j]), 1e-17);
       for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - dts * (fx[j - 1][i] - f0[i]) / h;
@@ -328,9 +331,12 @@ TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, do
 }
 
 // One Newton solve from `y` (seed on entry, root on exit), with the Jacobian reuse
-// above.  Returns the iterations used (chord iterations included), or -1.
+// above.  Returns the iterations used (chord iterations included), or -1.  `qb`, when
+// given, receives the C/O/e equilibrium at the last base point, the root's predecessor
+// (within 1e-12 relative of the root when the solve converges).
 TCG_FN int newton_solve(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
-                        double dts, double* y, double& xe_g, double& td_g, int maxit = 0) {
+                        double dts, double* y, double& xe_g, double& td_g, int maxit = 0,
+                        Equil<double>* qb = nullptr) {
   const int nmax = (maxit > 0 && maxit < p.newton_max) ? maxit : p.newton_max;
   double Jk[3][3];
   bool reuse = false;
@@ -338,7 +344,7 @@ TCG_FN int newton_solve(const CellC<double>& c, const DevParams& p, double mu, d
   for (int it = 1; it <= nmax; ++it) {
     double rel;
     bool full;
-    const int r = newton_iter(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, Jk, reuse, rel, full);
+    const int r = newton_iter(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, Jk, reuse, rel, full, qb);
     if (r < 0) return -1;
     if (r > 0) return it;
     reuse = full && rel < JAC_REUSE && (!reuse || rel <= 0.5 * prev);
@@ -381,6 +387,27 @@ TCG_FN void finish_substep(const CellC<F>& cf, double muH, const DevParams& p, d
   Equil<F> q = equilibrium(cf, b1, F(s.xH2), F(s.xHp), F(s.xe));
   s.xe = double(q.xe); s.xCp = double(q.xCp); s.xCO = double(q.xCO);
   s.mu = muH / (1.1 + s.xe - s.xH2);
+  s.t = last ? dt : s.t + dts;
+}
+
+// Accepts the root y of a substep whose last FP64 evaluation of f solved the C/O/e
+// equilibrium `q` at the root's predecessor y' (within 1e-12 of y relative for the FP64
+// Newton solve, within 1e-8 for the polish of the mixed one): that equilibrium sets
+// x_e, x_C+, x_CO and mu for the next substep instead of a new solve at y.  The
+// difference is that of the equilibrium between two states that close.  With the temperature floor active the
+// equilibrium is solved at the floored state instead.
+TCG_FN void finish_substep_q(const CellC<double>& c, const DevParams& p, double dt, double dts, bool last,
+                             const double* y, const Equil<double>& q, LaneState& s) {
+  if (!(y[0] >= p.T_floor / s.mu)) {
+    finish_substep<double>(c, c.muH, p, dt, dts, last, y, s);
+    return;
+  }
+  s.nsub += 1;
+  s.Tmu = y[0];
+  s.xH2 = y[1];
+  s.xHp = y[2];
+  s.xe = q.xe; s.xCp = q.xCp; s.xCO = q.xCO;
+  s.mu = c.muH / (1.1 + s.xe - s.xH2);
   s.t = last ? dt : s.t + dts;
 }
 
@@ -439,14 +466,14 @@ TCG_FN void picard_predictor(const CellC<double>& c, const DevParams& p, double 
 // fails, from the predictor above (flagging ST_PREDICTOR).  Returns the iterations of
 // the successful solve, or -1.
 TCG_FN int solve_from_start64(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
-                              double dts, double* y, double& xe_g, double& td_g, int& status) {
+                              double dts, double* y, double& xe_g, double& td_g, int& status, Equil<double>* qb) {
   y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2];
-  int it = newton_solve(c, p, mu, Kinv, yn, dts, y, xe_g, td_g);
+  int it = newton_solve(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, 0, qb);
   if (it >= 0) return it;
   status |= ST_PREDICTOR;
   picard_predictor(c, p, mu, Kinv, yn, dts, y, xe_g, td_g);
   if (!finite3(y[0], y[1], y[2])) return -1;
-  return newton_solve(c, p, mu, Kinv, yn, dts, y, xe_g, td_g);
+  return newton_solve(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, 0, qb);
 }
 
 // A seeded Newton solve that has not converged after this many iterations is abandoned
@@ -465,20 +492,21 @@ TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double d
   const double Kinv = 1.0 / c.K;
   double y[3] = {yn[0], yn[1], yn[2]};
   int it = -1;
+  Equil<double> qb;
   if (seed) {
     y[0] = seed[0]; y[1] = seed[1]; y[2] = seed[2];
     double xg = xe_g, tg = td_g;
-    it = newton_solve(c, p, s.mu, Kinv, yn, dts, y, xg, tg, SEED_MAXIT);
+    it = newton_solve(c, p, s.mu, Kinv, yn, dts, y, xg, tg, SEED_MAXIT, &qb);
     if (it >= 0) { xe_g = xg; td_g = tg; }
   }
-  if (it < 0) it = solve_from_start64(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status);
+  if (it < 0) it = solve_from_start64(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status, &qb);
   int halv = 0;
   while (it < 0 && halv < 30) {
     s.status |= ST_NEWTON;
     dts *= 0.5;
     last = false;
     ++halv;
-    it = solve_from_start64(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status);
+    it = solve_from_start64(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status, &qb);
   }
   if (it < 0) {
     s.status |= ST_NONFIN;
@@ -486,7 +514,7 @@ TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double d
     return;
   }
   s.iters += it;
-  finish_substep<double>(c, c.muH, p, dt, dts, last, y, s);
+  finish_substep_q(c, p, dt, dts, last, y, qb, s);
 }
 
 // Substep length of Sec. 6.1 from the FP64 source terms at the substep start.
@@ -590,25 +618,31 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
   return -1;
 }
 
-// FP64 polish of the mixed iteration's root: Newton corrections with the residual
-// evaluated entirely in FP64 and the last (FP32-built) Jacobian.  The FP32 root is
-// off the FP64 one by the FP32 rounding floor of f (~1e-6 relative in T near stiff
+// FP64 polish of the mixed iteration's root: chord corrections with the residual
+// evaluated entirely in FP64 and the last (FP32-built) Jacobian.  The FP32 root is off
+// the FP64 one by the FP32 rounding floor of f (~1e-6 relative in T near stiff
 // equilibria, where H is a small difference of large terms), and the scheme can
-// amplify such errors a hundredfold over a step, so every substep is polished.  The
-// chord iteration contracts by the Jacobian's relative error (<~0.1), so a correction
-// below 1e-8 relative leaves an error below ~1e-9: accept then, after at most five.
-// (Accepting at 1e-7 left one of 4096 random-state cells at 1.04e-5 in T after 86
-// substeps; at 1e-8, 2.5e-6.  Five corrections instead of three also send fewer
-// substeps to the FP64 fallback: 47 instead of 152 of those 4096 cells.)
-// Returns false if that does not happen.
+// amplify such errors a hundredfold over a step, so every substep is polished.
+// A chord iteration contracts by the Jacobian's relative error rho (~1e-3 for the FP32
+// forward differences of relative step 1e-3, worse near stiff equilibria), so after a
+// correction d_k the remaining error is about rho d_k / (1 - rho), with rho estimated as
+// d_k / d_(k-1).  Accepted when that estimate is below 1e-9 relative (abundances
+// relative to max(x, 1e-4)), or when a correction is itself below 1e-8 (on the slab the
+// first correction has a median of 3e-8 and rho a median of 0.015, 0.11 at the 90th
+// percentile); after at most five corrections, otherwise the FP64 solver takes the
+// substep.  Measured on 4 x 4096 random-state cells, largest error in T against the
+// FP64 oracle after one step, by the threshold for a single correction: 1e-7: 1.05e-5
+// (1.13 corrections per slab substep); 3e-8: 7.3e-6 (1.46); 1e-8: 4.6e-6 (1.83).
+// `qlast` receives the C/O/e equilibrium of the last FP64 evaluation.
 TCG_FN bool polish64(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
-                     double dts, double* y, const double J[3][3], double& xe_g, double& td_g) {
+                     double dts, double* y, const double J[3][3], double& xe_g, double& td_g, Equil<double>& qlast) {
+  double prev = -1.0;
   for (int it = 0; it < 5; ++it) {
     TCG_COUNT_D(polish_it);
     ChemT<double> b = chem_T(c, mu * y[0], p.flags);
     CoolT<double> k = cool_T(c, b, p.flags);
     double f0[3];
-    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0);
+    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, &qlast);
     double Jw[3][3], rhs[3], d[3];
     for (int i = 0; i < 3; ++i) {
       rhs[i] = -(y[i] - yn[i] - dts * f0[i]);
@@ -618,17 +652,28 @@ TCG_FN bool polish64(const CellC<double>& c, const DevParams& p, double mu, doub
     double st[3];
     const bool full = damped_step(y, d, st);
     double nrm = 0.0;
-    for (int i = 0; i < 3; ++i) nrm = fmax(nrm, fabs(st[i]) / (1e-8 * fabs(y[i]) + ((i == 0) ? 1e-300 : 1e-12)));
+    for (int i = 0; i < 3; ++i) nrm = fmax(nrm, fabs(st[i]) / (fabs(y[i]) + ((i == 0) ? 1e-300 : 1e-4)));
     if (!finite3(y[0], y[1], y[2])) return false;
-    if (full && nrm <= 1.0) return true;
+    if (!full) {
+      prev = -1.0;
+      continue;
+    }
+    if (nrm <= 1e-8) return true;
+    if (prev > 0.0) {
+      const double rho = nrm / prev;
+      if (rho < 0.5 && rho * nrm <= 1e-9 * (1.0 - rho)) return true;
+    }
+    prev = nrm;
   }
   return false;
 }
 
 // One mixed-precision substep.  FP64 work: the source terms at the substep start that
-// set its length (Sec. 6.1; the length decides where the trajectory is sampled, and a
-// 1e-6 error in it shifts every later state in time), the polish of the root, and the
-// C/O/e equilibrium that sets mu at the end.  FP32 work: every Newton iteration before
+// set its length (Sec. 6.1; the length decides where the trajectory is sampled: FP32
+// heating and cooling sums are off by up to ~5e-5 relative, and a length that far off
+// moved hot cells cooling through the Lyman-alpha peak by 1e-3 in T after ~70
+// substeps), and the polish of the root, whose last evaluation also gives the C/O/e
+// equilibrium that sets mu at the end (finish_substep_q).  FP32 work: every Newton iteration before
 // the polish and the Jacobian.  The solve starts from `seed` when given, else from the
 // start state.
 TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<float>& cf, const DevParams& p, double dt,
@@ -646,10 +691,11 @@ TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<float>& cf, 
     y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2];
     it = newton_mixed(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, J, polish);
   }
+  Equil<double> qlast;
   if (it >= 0) {
     if (polish) s.status |= ST_POLISH;
     double xg = double(xe_g), tg = double(td_g);
-    if (!polish64(c, p, s.mu, Kinv, yn, dts, y, J, xg, tg)) it = -1;
+    if (!polish64(c, p, s.mu, Kinv, yn, dts, y, J, xg, tg, qlast)) it = -1;
   }
   if (it < 0) {
     // The plain FP64 solver finishes this substep (same length, same start state).
@@ -658,7 +704,7 @@ TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<float>& cf, 
     solve_substep64(c, p, dt, dts, last, s, xg, tg);
   } else {
     s.iters += it;
-    finish_substep<double>(c, c.muH, p, dt, dts, last, y, s);
+    finish_substep_q(c, p, dt, dts, last, y, qlast, s);
   }
   xe_g = float(s.xe);
 }
