@@ -104,11 +104,19 @@ def job_throughput(ncell_per_rank: int, ws: int, steps: int, ms: float) -> float
 
 def work_per_cell():
     """FP64 operations per cell by class (add, mul, div, sqrt, exp, log) of one step on
-    the slab, per mode, counted from the library's own step functions
-    (paper_2210_08024_gb300/work.py)."""
+    the slab, per mode (and the mixed mode's FP32 operations), counted from the library's
+    own step functions (paper_2210_08024_gb300/work.py)."""
     path = os.path.join(ROOT, "paper_2210_08024_gb300", "work_slab128.json")
     with open(path) as fh:
         return json.load(fh)["per_cell"]
+
+
+def algorithmic_per_cell():
+    """Substeps, source-term evaluations and iterations per slab cell of each mode
+    (the method's own work knobs, counted like work_per_cell)."""
+    path = os.path.join(ROOT, "paper_2210_08024_gb300", "work_slab128.json")
+    with open(path) as fh:
+        return json.load(fh)["algorithmic"]
 
 
 MODE_WORK = {"paper": "mode0", "newton": "mode1", "mixed": "mode2", "newton_seeded": "mode1", "mixed_seeded": "mode2"}
@@ -173,7 +181,7 @@ def measure_peaks(tc, torch):
     rates = {}
     for name, kind, it in (("fma", 0, iters), ("exp", 2, iters // 16), ("log", 3, iters // 16),
                            ("sqrt", 4, iters // 8), ("div", 5, iters // 8), ("pow", 6, iters // 32),
-                           ("fma32", 1, iters * 8)):
+                           ("fma32", 1, iters * 8), ("mufu", 8, iters * 2)):
         tc.tc_peak_launch(kind, grid, block, it, sink)
         torch.cuda.synchronize()
         best = None
@@ -190,7 +198,8 @@ def measure_peaks(tc, torch):
     weights = {"add": 1.0, "mul": 1.0, "cmp": 0.0}
     for k in ("div", "sqrt", "exp", "log", "pow"):
         weights[k] = fma / rates[k]
-    return {"fp64_fma_per_s": fma, "fp32_fma_per_s": rates["fma32"], "rates": rates, "weights": weights}
+    return {"fp64_fma_per_s": fma, "fp32_fma_per_s": rates["fma32"], "mufu_per_s": rates["mufu"], "rates": rates,
+            "weights": weights}
 
 
 def flops_per_cell(counts: dict, weights: dict) -> float:
@@ -238,6 +247,9 @@ def run_gpu(args):
         if "seeded" in mname:
             st.load_mlp(blob)
         f = tc.make_fields(dev)
+        # launch shape: the library's autotuner times its candidates on this workload
+        # (on a scratch copy of the state) before the timed region
+        shape = tc.tc_autotune(st.h, f, DT, stream)
         for _ in range(args.warmup):
             restore()
             tc.tc_step(st.h, f, DT, stream)
@@ -271,7 +283,7 @@ def run_gpu(args):
         results[mname] = {"ms_per_step": ms / args.steps, "kernel_ms": float(np.mean(kms)),
                           "value": job_throughput(ncell, ws, args.steps, ms), "launches": launches,
                           "cells_not_ok": nbad, "newton_iters_per_cell": float(dev["iters"].double().mean().item()),
-                          "mode_id": mode_ids[mname]}
+                          "launch_shape": shape, "mode_id": mode_ids[mname]}
         st.close()
 
     head = modes[0]
@@ -280,7 +292,7 @@ def run_gpu(args):
     drivers = None
     if rank == 0 and not args.no_drivers:
         drivers = {"onezone": run_onezone(args, tc, torch, stream), "sixray": run_sixray(args, tc, torch, stream, peaks),
-                   "pdr": run_pdr(args, tc, torch, stream)}
+                   "pdr": run_pdr(args, tc, torch, stream), "config1_latency": run_latency(args, tc, torch, stream)}
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -289,6 +301,39 @@ def run_gpu(args):
     out = report(args, results, head, ncell, peaks, e2e, clocks, cells, ws)
     out["drivers"] = drivers
     out["second_step_cost_hint"] = hint
+    return out
+
+
+def run_latency(args, tc, torch, stream):
+    """The 4096 random states of config 1 (one step of 1e4 yr): a launch far too small to
+    fill the GPU, whose time is the latency of its slowest cells.  Plain FP64 and mixed,
+    one lane per cell against the warp-cooperative kernels (four lanes per cell, the
+    library's automatic choice for this size)."""
+    cells = synthgen.cells_4096()
+    dev = tc.to_device(cells)
+    pristine = {k: dev[k].clone() for k in STATE_KEYS}
+    out = {"workload": "4096 random states (log n in [-2,4], log T in [1,7]), dt = 1e4 yr"}
+    for mname, mode in (("newton", tc.TC_MODE_NEWTON_FP64), ("mixed", tc.TC_MODE_MIXED)):
+        row = {}
+        for lpc in (1, 4):
+            st = tc.Stepper(mode, lanes_per_cell=lpc)
+            f = tc.make_fields(dev)
+            times = []
+            for r in range(6):
+                for k in STATE_KEYS:
+                    dev[k].copy_(pristine[k])
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                tc.tc_step(st.h, f, DT, stream)
+                e1.record(stream)
+                e1.synchronize()
+                if r > 0:
+                    times.append(e0.elapsed_time(e1))
+            st.close()
+            ms = float(np.median(times))
+            row["lanes_per_cell_%d" % lpc] = {"ms": ms, "cell_updates_per_s": cells["n"].size / (ms * 1e-3)}
+        row["speedup_4_over_1"] = row["lanes_per_cell_1"]["ms"] / row["lanes_per_cell_4"]["ms"]
+        out[mname] = row
     return out
 
 
@@ -530,14 +575,19 @@ def report(args, results, head, ncell, peaks, e2e, clocks, cells, ws):
     # counts of the library's own step, weighted by the FMA-slot cost of each operation
     # class measured in this run) over the CUDA-event duration of the launch.
     work = work_per_cell()
+    algo = algorithmic_per_cell()
     r = results[head]
     roofline = None
     if peaks is not None:
         roofline = roofline_of(work, r, head, ncell, peaks)
+        roofline["algorithmic_per_cell"] = algo[MODE_WORK[head]]
         for name, rr in results.items():
             rl = roofline_of(work, rr, name, ncell, peaks)
             rr["fp64_roofline_frac"] = rl["frac"]
             rr["fp64_tflops"] = rl["achieved"]
+            rr["algorithmic_per_cell"] = algo[MODE_WORK[name]]
+            if MODE_WORK[name] == "mode2":
+                rr["fp32_pipes"] = fp32_fractions(work["mode2_fp32"], rr, ncell, peaks)
     cpu = None if args.no_cpu_baseline else cpu_baseline(cells, head)
     out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
@@ -553,9 +603,25 @@ def report(args, results, head, ncell, peaks, e2e, clocks, cells, ws):
            "peaks": None if peaks is None else {
                "fp64_tflops": 2.0 * peaks["fp64_fma_per_s"] / 1e12,
                "fp32_tflops": 2.0 * peaks["fp32_fma_per_s"] / 1e12,
+               "mufu_ops_per_s": peaks["mufu_per_s"],
                "fma_slot_weights": peaks["weights"]},
            "cpu_baseline": cpu}
     return out
+
+
+def fp32_fractions(w32, r, ncell, peaks):
+    """FP32 side of a mixed launch: FP32 flops (add and multiply, plus the multiply that
+    accompanies each approximate exp, log, sqrt and divide) against the measured FP32 FMA
+    rate, and MUFU operations (one per exp, log, sqrt and divide of the fast-math build)
+    against the measured MUFU rate.  The counts are the slab's per-cell FP32 work
+    (work_slab128.json, mode2_fp32) times the cells of the launch."""
+    t = r["kernel_ms"] * 1e-3
+    special = sum(w32[k] for k in ("div", "sqrt", "exp", "log"))
+    fl = (w32["add"] + w32["mul"] + special) * ncell
+    mufu = special * ncell
+    return {"fp32_tflops": fl / t / 1e12, "fp32_frac": fl / t / (2.0 * peaks["fp32_fma_per_s"]),
+            "mufu_ops_per_s": mufu / t, "mufu_frac": mufu / t / peaks["mufu_per_s"],
+            "work": "FP32 ops per cell of the library's mixed step (work_slab128.json, mode2_fp32) x %d cells" % ncell}
 
 
 def roofline_of(work, r, mode, ncell, peaks):

@@ -77,7 +77,7 @@ typedef struct tc_params {
   int mode;                    /* TC_MODE_* */
   unsigned flags;              /* TC_CONST_KGR | TC_NO_ROVIB | TC_NO_CIE */
   double newton_rtol_mixed;    /* step tolerance of the FP32 Newton iterations of the mixed modes; default 1e-6
-                                  (the FP64 polish then brings each root to 1e-7 relative) */
+                                  (the FP64 polish then brings each root to ~1e-9 relative) */
   int block;                   /* threads per block (0 = autotuned/default) */
   int blocks_per_sm;           /* resident blocks per SM for the persistent grid (0 = occupancy) */
   int order_cells;             /* 1 (default): hand cells to the persistent kernel in decreasing order of
@@ -87,6 +87,15 @@ typedef struct tc_params {
                                   longest cells then no longer finish last and warps hold cells of
                                   similar cost); needs 5 bytes of device workspace per cell, grown by
                                   cudaMalloc.  0: cells in index order. */
+  int lanes_per_cell;          /* lanes that advance one cell together (the library's scheduling, no
+                                  counterpart in the paper; results agree to rounding): 1, or 4 for the
+                                  warp-cooperative kernels of modes TC_MODE_NEWTON_FP64 and TC_MODE_MIXED,
+                                  whose four lanes evaluate the four points of each forward-difference
+                                  Jacobian at once (tc_step and tc_step_host only; other modes and
+                                  tc_step_batch use 1).  0 (default): 4 when the cells times 4 fit the
+                                  cooperative kernel's resident lanes at once (launches too small to fill
+                                  the GPU, whose time is the latency of the slowest cells), else 1, unless
+                                  tc_autotune has recorded a choice for the launch's size class. */
 } tc_params;
 
 typedef struct tc_fields {
@@ -140,6 +149,30 @@ int tc_step(tc_handle *h, const tc_fields *f, double dt_s, void *stream);
  * descriptors (1 <= nbox <= 64), read before the call returns.  Returns TC_EINVAL for a
  * bad count or descriptor, TC_ECUDA if capture or launch fails. */
 int tc_step_batch(tc_handle *h, const tc_fields *boxes, int nbox, double dt_s, void *stream);
+
+/* Launch shape chosen by tc_autotune (the library's scheduling; the paper has no
+ * counterpart). */
+typedef struct tc_tune_choice {
+  int block;           /* threads per block */
+  int blocks_per_sm;   /* resident blocks per SM of the persistent grid (0 = occupancy limit) */
+  int lanes_per_cell;  /* 1, or 4 for the warp-cooperative kernels */
+  float ms;            /* time of one step of *f in that shape */
+} tc_tune_choice;
+
+/* Autotuner of the step launch.  Times one step of the cells of *f (device pointers, as
+ * for tc_step) in every candidate shape -- 32, 64 or 128 threads per block, the occupancy
+ * limit or 4 resident blocks per SM, and for modes TC_MODE_NEWTON_FP64 and TC_MODE_MIXED
+ * one or four lanes per cell (four only when the cooperative kernel holds the cells in
+ * at most 8 waves of its resident lanes) -- with CUDA events on `stream`, each candidate
+ * once, or three times (fastest kept) when one step takes under 20 ms, and records the fastest
+ * for the size class floor(log2(ncell)) in the handle: later tc_step and tc_step_host
+ * calls of that size class whose tc_params leave block, blocks_per_sm and
+ * lanes_per_cell at 0 use it.  The candidates advance a scratch copy of T, x_h2 and
+ * x_hp (allocated here by cudaMalloc and freed before returning): *f is not modified.
+ * Synchronises `stream`; not for use while `stream` is being captured.  Writes the
+ * choice to *best.  Returns TC_EINVAL for bad fields, ncell < 1 or a bad dt_s,
+ * TC_ENOMLP for a seeded mode without weights, TC_ENOMEM, or TC_ECUDA. */
+int tc_autotune(tc_handle *h, const tc_fields *f, double dt_s, void *stream, tc_tune_choice *best);
 
 /* Like tc_step but every pointer in *f is a HOST pointer: the call copies inputs to the
  * device, runs the step, copies T, x_h2, x_hp (and the optional outputs) back and

@@ -9,6 +9,8 @@
  *   kind 2: FP64 exp()                   kind 3: FP64 log()
  *   kind 4: FP64 sqrt()                  kind 5: FP64 division
  *   kind 6: FP64 pow(x, y)               kind 7: FP32 expf()
+ *   kind 8: FP32 __expf(), the approximate exponential of the fast-math mixed kernels:
+ *           one MUFU ex2 per operation, so its rate is the MUFU pipe's
  * `sink` is a device buffer of grid * block doubles that receives the chain results
  * (written so the compiler cannot drop the work).  Returns TC_OK, TC_EINVAL or TC_ECUDA.
  */

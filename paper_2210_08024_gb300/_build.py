@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtc_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["tc_api.cu", "tc_onezone.cu", "tc_sixray.cu", "tc_pdr.cu", "tc_order.cu", "tc_k_paper.cu", "tc_k_newton.cu", "tc_k_mixed.cu", "tc_mlp.cu", "tc_peak.cu",
-           "tc_static.cu", "tc_k_seeded3.cu", "tc_k_seeded4.cu"]
+           "tc_static.cu", "tc_k_seeded3.cu", "tc_k_seeded4.cu", "tc_k_newton_coop.cu", "tc_k_mixed_coop.cu"]
 
 
 def nvcc() -> str:
@@ -35,7 +35,7 @@ def _flags():
 # approximate intrinsics (exp, log, divide; flush-to-zero).  This changes no FP64
 # operation.  Measured on the 128^3 slab: mixed 250 -> 215 ms, mixed + seed 295 ->
 # 238 ms, with the same iteration counts and the same parity results.
-FAST_FP32 = {"tc_k_mixed.cu", "tc_k_seeded3.cu"}
+FAST_FP32 = {"tc_k_mixed.cu", "tc_k_seeded3.cu", "tc_k_mixed_coop.cu"}
 
 
 def _compile(src: str) -> tuple[str, str]:

@@ -27,6 +27,17 @@ int occupancy_mode3_impl(int block);
 int occupancy_mode4_impl(int block);
 }  // namespace tcg
 
+constexpr int TUNE_CLASSES = 48;
+
+static int size_class(long long n) {
+  int c = 0;
+  while (n > 1 && c < TUNE_CLASSES - 1) {
+    n >>= 1;
+    ++c;
+  }
+  return c;
+}
+
 struct tc_handle {
   tc_params p;
   int device = 0;
@@ -58,6 +69,10 @@ struct tc_handle {
   unsigned* d_ohist = nullptr;
   unsigned* d_order = nullptr;
   size_t order_cells = 0;
+  // launch shapes recorded by tc_autotune, by size class floor(log2(ncell))
+  struct Tuned {
+    int valid, block, blocks_per_sm, lanes_per_cell;
+  } tuned[TUNE_CLASSES] = {};
   // driver workspace (tc_eq_curves, tc_pdr): per-cell arrays and the parameter arrays
   double* d_eq = nullptr;
   int* d_eqi = nullptr;
@@ -208,24 +223,47 @@ static int kernel_mode(int mode) {
   }
 }
 
-static void launch_shape(tc_handle* h, int kmode, long long ntotal, int* grid, int* block) {
-  int b = h->p.block > 0 ? h->p.block : 128;
+static int coop_occupancy(int kmode, int block) {
+  return (kmode == 1) ? tcg::occupancy_mode1_coop(block) : tcg::occupancy_mode2_coop(block);
+}
+
+// Launch shape of one step launch: threads per block, grid and lanes per cell.  Explicit
+// tc_params values win; otherwise the shape tc_autotune recorded for the launch's size
+// class; otherwise 128 threads, the occupancy limit, and four lanes per cell when every
+// cell's four lanes fit the cooperative kernel's resident lanes at once (modes 1 and 2,
+// one box).  The persistent grid never exceeds the blocks that hold one lane per cell
+// lane.
+struct Shape {
+  int grid, block, lpc;
+};
+static Shape launch_shape(tc_handle* h, int kmode, bool batch, long long ntotal) {
+  int b = h->p.block, per_sm = h->p.blocks_per_sm, lpc = h->p.lanes_per_cell;
+  const bool coop_ok = (kmode == 1 || kmode == 2) && !batch;
+  const tc_handle::Tuned& t = h->tuned[size_class(ntotal)];
+  if (t.valid && !batch && b <= 0 && per_sm <= 0 && lpc <= 0) {
+    b = t.block;
+    per_sm = t.blocks_per_sm;
+    lpc = t.lanes_per_cell;
+  }
+  if (b <= 0) b = 128;
   if (b > 128) b = 128;  // kernels are compiled with __launch_bounds__(128)
   b = (b / 32) * 32;
   if (b < 32) b = 32;
-  int per_sm = h->p.blocks_per_sm;
+  if (!coop_ok) lpc = 1;
+  if (lpc <= 0) lpc = (ntotal * 4 <= (long long)h->num_sms * coop_occupancy(kmode, b) * b) ? 4 : 1;
+  if (lpc != 4) lpc = 1;
   if (per_sm <= 0) {
-    per_sm = (kmode == 0) ? tcg::occupancy_mode0_impl(b)
+    per_sm = (lpc == 4) ? coop_occupancy(kmode, b)
+             : (kmode == 0) ? tcg::occupancy_mode0_impl(b)
              : (kmode == 1) ? tcg::occupancy_mode1_impl(b)
              : (kmode == 2) ? tcg::occupancy_mode2_impl(b)
              : (kmode == 3) ? tcg::occupancy_mode3_impl(b) : tcg::occupancy_mode4_impl(b);
   }
   long long g = (long long)h->num_sms * per_sm;
-  long long need = (ntotal + b - 1) / b;
+  long long need = (ntotal * lpc + b - 1) / b;
   if (g > need) g = need;
   if (g < 1) g = 1;
-  *grid = (int)g;
-  *block = b;
+  return Shape{(int)g, b, lpc};
 }
 
 // Grows the cost-ordering workspace to ncell cells (not while `st` is being captured).
@@ -260,8 +298,8 @@ static int enqueue(tc_handle* h, bool batch, const tcg::DevFields& f, long long 
   if (h->p.mode == TC_MODE_MIXED_SEEDED || h->p.mode == TC_MODE_NEWTON_FP64_SEEDED) {
     if (!h->d_mlp) return TC_ENOMLP;
   }
-  int grid, block;
-  launch_shape(h, kmode, ntotal, &grid, &block);
+  const Shape sh = launch_shape(h, kmode, batch, ntotal);
+  const int grid = sh.grid, block = sh.block;
   if (cudaMemsetAsync(h->d_cursor, 0, sizeof(unsigned long long), st) != cudaSuccess) return TC_ECUDA;
   tcg::DevParams dp = dev_params(h->p);
   // cost-ordered queue: only worth it when the launch holds more cells than a few warps
@@ -273,7 +311,9 @@ static int enqueue(tc_handle* h, bool batch, const tcg::DevFields& f, long long 
     dp.order = h->d_order;
   }
   cudaError_t e;
-  if (kmode == 0) e = tcg::launch_mode0(batch, f, h->d_boxes, dp, dt, h->d_cursor, ntotal, grid, block, st);
+  if (sh.lpc == 4 && kmode == 1) e = tcg::launch_mode1_coop(f, dp, dt, h->d_cursor, ntotal, grid, block, st);
+  else if (sh.lpc == 4 && kmode == 2) e = tcg::launch_mode2_coop(f, dp, dt, h->d_cursor, ntotal, grid, block, st);
+  else if (kmode == 0) e = tcg::launch_mode0(batch, f, h->d_boxes, dp, dt, h->d_cursor, ntotal, grid, block, st);
   else if (kmode == 1) e = tcg::launch_mode1(batch, f, h->d_boxes, dp, dt, h->d_cursor, ntotal, grid, block, st);
   else if (kmode == 2) e = tcg::launch_mode2(batch, f, h->d_boxes, dp, dt, h->d_cursor, ntotal, grid, block, st);
   else if (kmode == 3)
@@ -294,6 +334,86 @@ int tc_step(tc_handle* h, const tc_fields* f, double dt_s, void* stream) {
   if (!(dt_s >= 0.0) || !isfinite(dt_s)) return TC_EINVAL;
   if (f->ncell == 0) return TC_OK;
   return enqueue(h, false, dev_fields(f), f->ncell, dt_s, (cudaStream_t)stream);
+}
+
+int tc_autotune(tc_handle* h, const tc_fields* f, double dt_s, void* stream, tc_tune_choice* best) {
+  if (!h || !best) return TC_EINVAL;
+  int rc = check_fields(f);
+  if (rc != TC_OK) return rc;
+  if (f->ncell < 1 || !(dt_s >= 0.0) || !isfinite(dt_s)) return TC_EINVAL;
+  const int kmode = kernel_mode(h->p.mode);
+  if ((kmode == 3 || kmode == 4) && !h->d_mlp) return TC_ENOMLP;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = (size_t)f->ncell;
+  // Candidates run on a scratch copy of the state; the inputs are only read.
+  double* scratch = nullptr;
+  if (cudaMalloc(&scratch, 3 * n * sizeof(double)) != cudaSuccess) return TC_ENOMEM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaFree(scratch);
+    return TC_ECUDA;
+  }
+  tc_fields d = *f;
+  d.T = scratch;
+  d.x_h2 = scratch + n;
+  d.x_hp = scratch + 2 * n;
+  d.x_e = d.x_cp = d.x_co = nullptr;
+  d.nsub = d.status = d.newton_iters = nullptr;
+  const tc_params saved = h->p;
+  const tc_handle::Tuned told = h->tuned[size_class(f->ncell)];
+  h->tuned[size_class(f->ncell)].valid = 0;
+  // four lanes per cell only where the cooperative kernel holds the launch's cells in at
+  // most 8 waves of resident lanes (beyond that it is slower by construction)
+  const bool coop_ok = (kmode == 1 || kmode == 2) &&
+                       (long long)f->ncell * 4 <= 8LL * h->num_sms * coop_occupancy(kmode, 128) * 128;
+  const int blocks[3] = {32, 64, 128};
+  const int per_sms[2] = {0, 4};
+  const int lpcs[2] = {1, 4};
+  // One run in the default shape first (it also sets how often each candidate repeats).
+  auto run = [&](float* ms) -> int {
+    const double* src[3] = {f->T, f->x_h2, f->x_hp};
+    for (int k = 0; k < 3; ++k)
+      if (cudaMemcpyAsync(scratch + k * n, src[k], n * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return TC_ECUDA;
+    if (cudaEventRecord(e0, st) != cudaSuccess) return TC_ECUDA;
+    const int r = enqueue(h, false, dev_fields(&d), f->ncell, dt_s, st);
+    if (r != TC_OK) return r;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return TC_ECUDA;
+    return (cudaEventElapsedTime(ms, e0, e1) == cudaSuccess) ? TC_OK : TC_ECUDA;
+  };
+  float ms0 = 0.f;
+  h->p.block = 0;
+  h->p.blocks_per_sm = 0;
+  h->p.lanes_per_cell = 0;
+  rc = run(&ms0);
+  const int reps = (rc == TC_OK && ms0 < 20.f) ? 3 : 1;
+  tc_tune_choice bestc = {0, 0, 0, 3.4e38f};
+  for (int ib = 0; ib < 3 && rc == TC_OK; ++ib)
+    for (int ip = 0; ip < 2 && rc == TC_OK; ++ip)
+      for (int il = 0; il < (coop_ok ? 2 : 1) && rc == TC_OK; ++il) {
+        h->p.block = blocks[ib];
+        h->p.blocks_per_sm = per_sms[ip];
+        h->p.lanes_per_cell = lpcs[il];
+        float tmin = 3.4e38f;
+        for (int r = 0; r < reps && rc == TC_OK; ++r) {
+          float ms = 0.f;
+          rc = run(&ms);
+          if (ms < tmin) tmin = ms;
+        }
+        if (rc == TC_OK && tmin < bestc.ms) bestc = tc_tune_choice{blocks[ib], per_sms[ip], lpcs[il], tmin};
+      }
+  h->p = saved;
+  if (rc == TC_OK) {
+    h->tuned[size_class(f->ncell)] = tc_handle::Tuned{1, bestc.block, bestc.blocks_per_sm, bestc.lanes_per_cell};
+    *best = bestc;
+  } else {
+    h->tuned[size_class(f->ncell)] = told;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(scratch);
+  return rc;
 }
 
 int tc_step_host(tc_handle* h, const tc_fields* f, double dt_s, void* stream) {

@@ -53,6 +53,63 @@ __device__ __forceinline__ long long claim_cells(unsigned long long* cursor) {
   return (long long)base + __popc(mask & ((1u << lane) - 1u));
 }
 
+// Several lanes per cell (LPC = 4, the warp-cooperative kernels): a cell is owned by LPC
+// consecutive lanes that hold identical copies of its state and run the same control
+// flow; they split the independent function evaluations of a Newton iteration and
+// exchange the results by shuffles over the cell's lane mask.  Every lane then forms the
+// same Jacobian and takes the same step, so the copies stay identical.
+template <int LPC>
+TCG_FN int lane_in_cell() {
+#ifdef __CUDA_ARCH__
+  return (int)(threadIdx.x & (unsigned)(LPC - 1));
+#else
+  return 0;
+#endif
+}
+
+// Value of v held by lane r of this lane's cell.
+template <int LPC>
+TCG_FN double from_lane(double v, int r) {
+#ifdef __CUDA_ARCH__
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned base = lane & ~(unsigned)(LPC - 1);
+  const unsigned mask = ((1u << LPC) - 1u) << base;
+  return __shfl_sync(mask, v, (int)(base + (unsigned)r));
+#else
+  return v;
+#endif
+}
+template <int LPC>
+TCG_FN float from_lane(float v, int r) {
+#ifdef __CUDA_ARCH__
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned base = lane & ~(unsigned)(LPC - 1);
+  const unsigned mask = ((1u << LPC) - 1u) << base;
+  return __shfl_sync(mask, v, (int)(base + (unsigned)r));
+#else
+  return v;
+#endif
+}
+
+// Work-queue claim for cells of LPC lanes: the first lane of the cell takes the next
+// index and hands it to the others by a shuffle over the cell's explicit lane mask
+// (__activemask could return part of a cell whose lanes are briefly apart, so the
+// claim does not aggregate over the warp).
+template <int LPC>
+__device__ __forceinline__ long long claim_cells_lpc(unsigned long long* cursor) {
+  if constexpr (LPC == 1) {
+    return claim_cells(cursor);
+  } else {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned base = lane & ~(unsigned)(LPC - 1);
+    const unsigned mask = ((1u << LPC) - 1u) << base;
+    unsigned long long v = 0;
+    if (lane == base) v = atomicAdd(cursor, 1ull);
+    v = __shfl_sync(mask, v, (int)base);
+    return (long long)v;
+  }
+}
+
 // Lane-resident state of the cell being advanced.
 struct LaneState {
   double t, Tmu, xH2, xHp, mu;
@@ -275,21 +332,57 @@ constexpr double JAC_REUSE = 1e-3;
 // test that every full step is below rtol |y_i|.  `rel` returns the step's largest
 // relative component and `full` whether no damping limit acted.  Returns 1 when
 // converged, 0 to continue, -1 on failure (singular Jacobian or a non-finite state).
+template <int LPC = 1>
 TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
                        double dts, double* y, double& xe_g, double& td_g, double (*Jk)[3], bool reuse,
                        double& rel, bool& full, Equil<double>* qb) {
   double f0[3], J[3][3];
-  ChemT<double> b = chem_T(c, mu * y[0], p.flags);
-  CoolT<double> k = cool_T(c, b, p.flags);
   if (reuse) {
     TCG_COUNT_D(chord64_it);
+    ChemT<double> b = chem_T(c, mu * y[0], p.flags);
+    CoolT<double> k = cool_T(c, b, p.flags);
     feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, qb);
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) J[i][j] = Jk[i][j];
+  } else if constexpr (LPC == 4) {
+    TCG_COUNT_D(newton64_it);
+    // Warp-cooperative forward-difference Jacobian: lane q of the cell evaluates f at the
+    // base point (q = 0) or with x_H2 (q = 1), x_H+ (q = 2) or T_mu (q = 3) perturbed,
+    // each from the same x_e and T_d guesses; the four results are exchanged.
+    const int q = lane_in_cell<4>();
+    const double h0 = 1e-7 * y[0];
+    const double h1 = fmax(1e-7 * fabs(y[1]), 1e-17), h2 = fmax(1e-7 * fabs(y[2]), 1e-17);
+    double fq[3];
+    Equil<double> qq;
+    double xg = xe_g, tg = td_g;
+    {
+      ChemT<double> b = chem_T(c, mu * ((q == 3) ? y[0] + h0 : y[0]), p.flags);
+      CoolT<double> k = cool_T(c, b, p.flags);
+      feval64(c, b, k, y[1] + ((q == 1) ? h1 : 0.0), y[2] + ((q == 2) ? h2 : 0.0), Kinv, xg, tg, fq, &qq);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      f0[i] = from_lane<4>(fq[i], 0);
+      const double f1 = from_lane<4>(fq[i], 1), f2 = from_lane<4>(fq[i], 2), fT = from_lane<4>(fq[i], 3);
+      J[i][1] = ((i == 1) ? 1.0 : 0.0) - dts * (f1 - f0[i]) / h1;
+      J[i][2] = ((i == 2) ? 1.0 : 0.0) - dts * (f2 - f0[i]) / h2;
+      J[i][0] = ((i == 0) ? 1.0 : 0.0) - dts * (fT - f0[i]) / h0;
+    }
+    xe_g = from_lane<4>(xg, 0);
+    td_g = from_lane<4>(tg, 0);
+    if (qb) {
+      qb->xe = from_lane<4>(qq.xe, 0);
+      qb->xCp = from_lane<4>(qq.xCp, 0);
+      qb->xCO = from_lane<4>(qq.xCO, 0);
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Jk[i][j] = J[i][j];
   } else {
     TCG_COUNT_D(newton64_it);
     // evaluation order: x_H2 column, x_H+ column, base point (all at the base T), then
     // the T_mu column, so the temperature blocks are built twice per iteration.
+    ChemT<double> b = chem_T(c, mu * y[0], p.flags);
+    CoolT<double> k = cool_T(c, b, p.flags);
     double fx[2][3];
 #pragma unroll 1
     for (int j = 1; j < 3; ++j) {
@@ -334,6 +427,7 @@ TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, do
 // above.  Returns the iterations used (chord iterations included), or -1.  `qb`, when
 // given, receives the C/O/e equilibrium at the last base point, the root's predecessor
 // (within 1e-12 relative of the root when the solve converges).
+template <int LPC = 1>
 TCG_FN int newton_solve(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
                         double dts, double* y, double& xe_g, double& td_g, int maxit = 0,
                         Equil<double>* qb = nullptr) {
@@ -344,7 +438,7 @@ TCG_FN int newton_solve(const CellC<double>& c, const DevParams& p, double mu, d
   for (int it = 1; it <= nmax; ++it) {
     double rel;
     bool full;
-    const int r = newton_iter(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, Jk, reuse, rel, full, qb);
+    const int r = newton_iter<LPC>(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, Jk, reuse, rel, full, qb);
     if (r < 0) return -1;
     if (r > 0) return it;
     reuse = full && rel < JAC_REUSE && (!reuse || rel <= 0.5 * prev);
@@ -465,15 +559,16 @@ TCG_FN void picard_predictor(const CellC<double>& c, const DevParams& p, double 
 // One substep's FP64 Newton solve at length dts: from the start state, and if that
 // fails, from the predictor above (flagging ST_PREDICTOR).  Returns the iterations of
 // the successful solve, or -1.
+template <int LPC = 1>
 TCG_FN int solve_from_start64(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
                               double dts, double* y, double& xe_g, double& td_g, int& status, Equil<double>* qb) {
   y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2];
-  int it = newton_solve(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, 0, qb);
+  int it = newton_solve<LPC>(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, 0, qb);
   if (it >= 0) return it;
   status |= ST_PREDICTOR;
   picard_predictor(c, p, mu, Kinv, yn, dts, y, xe_g, td_g);
   if (!finite3(y[0], y[1], y[2])) return -1;
-  return newton_solve(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, 0, qb);
+  return newton_solve<LPC>(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, 0, qb);
 }
 
 // A seeded Newton solve that has not converged after this many iterations is abandoned
@@ -486,6 +581,7 @@ constexpr float SEED_MAX_DLOGT = 0.02f, SEED_MAX_DX = 0.02f;
 // given (the root is the same; a seeded solve that fails is retried from the start
 // state), else from the start state, then from the predictor; a substep that fails
 // from both is retried at half length (up to 30 times) and the cell flagged ST_NEWTON.
+template <int LPC = 1>
 TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double dt, double dts, bool last,
                             LaneState& s, double& xe_g, double& td_g, const double* seed = nullptr) {
   const double yn[3] = {s.Tmu, s.xH2, s.xHp};
@@ -496,17 +592,17 @@ TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double d
   if (seed) {
     y[0] = seed[0]; y[1] = seed[1]; y[2] = seed[2];
     double xg = xe_g, tg = td_g;
-    it = newton_solve(c, p, s.mu, Kinv, yn, dts, y, xg, tg, SEED_MAXIT, &qb);
+    it = newton_solve<LPC>(c, p, s.mu, Kinv, yn, dts, y, xg, tg, SEED_MAXIT, &qb);
     if (it >= 0) { xe_g = xg; td_g = tg; }
   }
-  if (it < 0) it = solve_from_start64(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status, &qb);
+  if (it < 0) it = solve_from_start64<LPC>(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status, &qb);
   int halv = 0;
   while (it < 0 && halv < 30) {
     s.status |= ST_NEWTON;
     dts *= 0.5;
     last = false;
     ++halv;
-    it = solve_from_start64(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status, &qb);
+    it = solve_from_start64<LPC>(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status, &qb);
   }
   if (it < 0) {
     s.status |= ST_NONFIN;
@@ -525,11 +621,12 @@ TCG_FN double substep_start64(const CellC<double>& c, const DevParams& p, double
   return substep_len(p, dt - s.t, c.K * s.Tmu, H0, CH2, CHp, last);
 }
 
+template <int LPC = 1>
 TCG_FN void substep_newton64(const CellC<double>& c, const DevParams& p, double dt, LaneState& s, double& xe_g,
                              double& td_g) {
   bool last;
   const double dts = substep_start64(c, p, dt, s, td_g, last);
-  solve_substep64(c, p, dt, dts, last, s, xe_g, td_g);
+  solve_substep64<LPC>(c, p, dt, dts, last, s, xe_g, td_g);
 }
 
 // ------------------------------------------------------------------ mode 2: mixed precision
@@ -557,6 +654,7 @@ TCG_FN void feval32(const CellC<float>& cf, const ChemT<float>& b, const CoolT<f
 // stopped contracting above that, at the FP32 rounding floor of f (below 1e-4
 // relative), which happens near stiff equilibria where H or C_s is a small difference
 // of large terms; or -1 if neither happened.  J holds the last Jacobian on return.
+template <int LPC = 1>
 TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, double Kinv, const double* yn,
                         double dts, double* y, float& xe_g, float& td_g, double J[3][3], bool& polish) {
   bool haveJ = false;
@@ -565,9 +663,37 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
   polish = false;
   for (int it = 1; it <= p.newton_max; ++it) {
     TCG_COUNT_D(newton32_it);
+    double f0[3];
+    bool coop = false;
+    if (LPC == 4 && !haveJ) {
+      // Warp-cooperative FP32 Jacobian: lane q evaluates f at the base point (q = 0) or
+      // with x_H2, x_H+ or T_mu perturbed (q = 1, 2, 3); the results are exchanged.
+      const int q = lane_in_cell<LPC>();
+      const double h0 = 1e-3 * y[0];
+      const double h1 = fmax(1e-3 * fabs(y[1]), 1e-12), h2 = fmax(1e-3 * fabs(y[2]), 1e-12);
+      float xg = xe_g, tg = td_g;
+      double fq[3];
+      {
+        ChemT<float> b = chem_T(cf, float(mu * ((q == 3) ? y[0] + h0 : y[0])), p.flags);
+        CoolT<float> k = cool_T(cf, b, p.flags);
+        feval32(cf, b, k, y[1] + ((q == 1) ? h1 : 0.0), y[2] + ((q == 2) ? h2 : 0.0), Kinv, xg, tg, fq);
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        f0[i] = from_lane<LPC>(fq[i], 0);
+        const double f1 = from_lane<LPC>(fq[i], 1), f2 = from_lane<LPC>(fq[i], 2), fT = from_lane<LPC>(fq[i], 3);
+        J[i][1] = ((i == 1) ? 1.0 : 0.0) - dts * (f1 - f0[i]) / h1;
+        J[i][2] = ((i == 2) ? 1.0 : 0.0) - dts * (f2 - f0[i]) / h2;
+        J[i][0] = ((i == 0) ? 1.0 : 0.0) - dts * (fT - f0[i]) / h0;
+      }
+      xe_g = from_lane<LPC>(xg, 0);
+      td_g = from_lane<LPC>(tg, 0);
+      haveJ = true;
+      coop = true;
+    }
+    if (!coop) {
     ChemT<float> b = chem_T(cf, float(mu * y[0]), p.flags);
     CoolT<float> k = cool_T(cf, b, p.flags);
-    double f0[3];
     feval32(cf, b, k, y[1], y[2], Kinv, xe_g, td_g, f0);
     if (!haveJ) {
 #pragma unroll 1
@@ -587,6 +713,7 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
       feval32(cf, bT, kT, y[1], y[2], Kinv, xg, tg, fT);
       for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - dts * (fT[i] - f0[i]) / h;
       haveJ = true;
+    }
     }
     double Jw[3][3], rhs[3], d[3];
     for (int i = 0; i < 3; ++i) {
@@ -676,6 +803,7 @@ TCG_FN bool polish64(const CellC<double>& c, const DevParams& p, double mu, doub
 // equilibrium that sets mu at the end (finish_substep_q).  FP32 work: every Newton iteration before
 // the polish and the Jacobian.  The solve starts from `seed` when given, else from the
 // start state.
+template <int LPC = 1>
 TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<float>& cf, const DevParams& p, double dt,
                                 double dts, bool last, LaneState& s, float& xe_g, float& td_g, double td64,
                                 const double* seed) {
@@ -685,11 +813,11 @@ TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<float>& cf, 
   if (seed) { y[0] = seed[0]; y[1] = seed[1]; y[2] = seed[2]; }
   double J[3][3];
   bool polish = false;
-  int it = newton_mixed(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, J, polish);
+  int it = newton_mixed<LPC>(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, J, polish);
   if (it < 0 && seed) {
     // a seed that did not lead to convergence: start again from the start state
     y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2];
-    it = newton_mixed(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, J, polish);
+    it = newton_mixed<LPC>(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, J, polish);
   }
   Equil<double> qlast;
   if (it >= 0) {
@@ -701,7 +829,7 @@ TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<float>& cf, 
     // The plain FP64 solver finishes this substep (same length, same start state).
     s.status |= ST_FALLBACK;
     double xg = s.xe, tg = td64;
-    solve_substep64(c, p, dt, dts, last, s, xg, tg);
+    solve_substep64<LPC>(c, p, dt, dts, last, s, xg, tg);
   } else {
     s.iters += it;
     finish_substep_q(c, p, dt, dts, last, y, qlast, s);
@@ -709,11 +837,12 @@ TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<float>& cf, 
   xe_g = float(s.xe);
 }
 
+template <int LPC = 1>
 TCG_FN void substep_mixed(const CellC<double>& c, const CellC<float>& cf, const DevParams& p, double dt,
                           LaneState& s, float& xe_g, float& td_g, double& td64) {
   bool last;
   const double dts = substep_start64(c, p, dt, s, td64, last);
-  substep_mixed_solve(c, cf, p, dt, dts, last, s, xe_g, td_g, td64, nullptr);
+  substep_mixed_solve<LPC>(c, cf, p, dt, dts, last, s, xe_g, td_g, td64, nullptr);
 }
 
 // ------------------------------------------------------------------ seeding (modes 3, 4)
@@ -759,11 +888,16 @@ TCG_FN bool mlp_seed(const MlpDev* __restrict__ w, seed_act_t* buf0, seed_act_t*
 //   4 blocks (128) 394 / 195,  5 (96) 375 / 174,  6 (80) 365 / 164,
 //   7 (72) 362 / 156,  8 (64) 363 / 152.
 constexpr int STEP_MIN_BLOCKS = 8;
+// The warp-cooperative kernels (four lanes per cell) serve launches too small to fill
+// the GPU, where the time is the latency of the slowest cells: 4 resident blocks (128
+// registers per thread) spill less.
+constexpr int STEP_MIN_BLOCKS_COOP = 4;
 
-template <int MODE, bool BATCH>
-__global__ void __launch_bounds__(128, STEP_MIN_BLOCKS) k_step(DevFields f1, const BoxTable* __restrict__ boxes, DevParams p,
-                                               double dt, unsigned long long* cursor, long long ntotal,
-                                               const MlpDev* __restrict__ mlp) {
+template <int MODE, bool BATCH, int LPC = 1>
+__global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_BLOCKS_COOP)
+    k_step(DevFields f1, const BoxTable* __restrict__ boxes, DevParams p, double dt, unsigned long long* cursor,
+           long long ntotal, const MlpDev* __restrict__ mlp) {
+  static_assert(LPC == 1 || ((MODE == 1 || MODE == 2) && !BATCH), "cooperative kernels: modes 1 and 2, one box");
   constexpr bool SEEDED = (MODE == 3 || MODE == 4);
   constexpr bool MIXED = (MODE == 2 || MODE == 3);
   const MlpDev* wsm = nullptr;
@@ -792,7 +926,7 @@ __global__ void __launch_bounds__(128, STEP_MIN_BLOCKS) k_step(DevFields f1, con
   bool have = false;
   while (true) {
     if (!have) {
-      long long gi = claim_cells(cursor);
+      long long gi = claim_cells_lpc<LPC>(cursor);
       if (gi >= ntotal) break;
       if (p.order) gi = (long long)p.order[gi];
       if (BATCH) {
@@ -850,9 +984,9 @@ __global__ void __launch_bounds__(128, STEP_MIN_BLOCKS) k_step(DevFields f1, con
       } else if constexpr (MODE == 0) {
         substep_paper(c, p, dt, s);
       } else if constexpr (MODE == 1) {
-        substep_newton64(c, p, dt, s, xe_g, td_g);
+        substep_newton64<LPC>(c, p, dt, s, xe_g, td_g);
       } else if constexpr (MODE == 2) {
-        substep_mixed(c, cf, p, dt, s, xe_gf, td_gf, td64);
+        substep_mixed<LPC>(c, cf, p, dt, s, xe_gf, td_gf, td64);
       } else {
         bool last;
         const double dts = substep_start64(c, p, dt, s, (MODE == 3) ? td64 : td_g, last);

@@ -12,6 +12,14 @@ cudaError_t launch_mode1(bool batch, const DevFields& f, const BoxTable* d_boxes
                          unsigned long long* cursor, long long ntotal, int grid, int block, cudaStream_t st);
 cudaError_t launch_mode2(bool batch, const DevFields& f, const BoxTable* d_boxes, const DevParams& p, double dt,
                          unsigned long long* cursor, long long ntotal, int grid, int block, cudaStream_t st);
+// Warp-cooperative variants of modes 1 and 2 (four lanes per cell, one box); `grid`
+// and `block` count threads, four per cell.
+cudaError_t launch_mode1_coop(const DevFields& f, const DevParams& p, double dt, unsigned long long* cursor,
+                              long long ntotal, int grid, int block, cudaStream_t st);
+cudaError_t launch_mode2_coop(const DevFields& f, const DevParams& p, double dt, unsigned long long* cursor,
+                              long long ntotal, int grid, int block, cudaStream_t st);
+int occupancy_mode1_coop(int block);
+int occupancy_mode2_coop(int block);
 // Seeded modes (3: mixed, 4: FP64 Newton); mlp points to the device weight blob.
 cudaError_t launch_mode3(bool batch, const DevFields& f, const BoxTable* d_boxes, const DevParams& p, double dt,
                          unsigned long long* cursor, long long ntotal, int grid, int block, cudaStream_t st,

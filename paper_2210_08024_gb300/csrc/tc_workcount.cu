@@ -195,13 +195,15 @@ int main(int argc, char** argv) {
     const wc::Calls& f = wc::calls[1];
     printf("  \"mode%d\": {\"substeps\": %.4f, \"fp64\": {\"chem_T\": %.4f, \"cool_T\": %.4f, \"equil\": %.4f, "
            "\"equil_it\": %.4f, \"dust\": %.4f, \"dust_it\": %.4f, \"source\": %.4f, \"newton64_it\": %.4f, "
-           "\"chord64_it\": %.4f, \"newton32_it\": %.4f, \"polish_it\": %.4f, \"substep_paper\": %.4f}, \"fp32\": {\"chem_T\": %.4f, "
-           "\"cool_T\": %.4f, \"equil_it\": %.4f, \"dust_it\": %.4f, \"source\": %.4f}}%s\n",
+           "\"chord64_it\": %.4f, \"newton32_it\": %.4f, \"polish_it\": %.4f, \"substep_paper\": %.4f, "
+           "\"picard_it\": %.4f}, \"fp32\": {\"chem_T\": %.4f, \"cool_T\": %.4f, \"equil\": %.4f, "
+           "\"equil_it\": %.4f, \"dust\": %.4f, \"dust_it\": %.4f, \"source\": %.4f}}%s\n",
            mode, (double)nsub / n, (double)k.chem_T / n, (double)k.cool_T / n, (double)k.equil / n,
            (double)k.equil_it / n, (double)k.dust / n, (double)k.dust_it / n, (double)k.source / n,
            (double)k.newton64_it / n, (double)k.chord64_it / n, (double)k.newton32_it / n, (double)k.polish_it / n,
-           (double)k.substep_paper / n, (double)f.chem_T / n, (double)f.cool_T / n, (double)f.equil_it / n,
-           (double)f.dust_it / n, (double)f.source / n, mode < 2 ? "," : "");
+           (double)k.substep_paper / n, (double)k.picard_it / n, (double)f.chem_T / n, (double)f.cool_T / n,
+           (double)f.equil / n, (double)f.equil_it / n, (double)f.dust / n, (double)f.dust_it / n,
+           (double)f.source / n, mode < 2 ? "," : "");
   }
   printf("}\n");
   return 0;

@@ -38,7 +38,13 @@ class tc_params(ctypes.Structure):
         ("block", ctypes.c_int),
         ("blocks_per_sm", ctypes.c_int),
         ("order_cells", ctypes.c_int),
+        ("lanes_per_cell", ctypes.c_int),
     ]
+
+
+class tc_tune_choice(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("lanes_per_cell", ctypes.c_int),
+                ("ms", ctypes.c_float)]
 
 
 _P = ctypes.c_void_p
@@ -114,6 +120,8 @@ def _load():
     L.tc_create.argtypes = [ctypes.POINTER(tc_params), ctypes.POINTER(ctypes.c_void_p)]
     L.tc_step.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_double, ctypes.c_void_p]
     L.tc_step_host.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_double, ctypes.c_void_p]
+    L.tc_autotune.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_double, ctypes.c_void_p,
+                              ctypes.POINTER(tc_tune_choice)]
     L.tc_step_batch.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_int, ctypes.c_double,
                                 ctypes.c_void_p]
     L.tc_load_mlp.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
@@ -239,6 +247,14 @@ def make_host_fields(arrs: dict, Zg: float = 1.0, Zd: float = 1.0) -> tc_fields:
     return f
 
 
+def tc_autotune(h, fields: tc_fields, dt: float, stream=None) -> dict:
+    """Times the candidate launch shapes on the cells of `fields` (not modified) and
+    records the fastest in the handle for their size class; returns it."""
+    c = tc_tune_choice()
+    _check(lib.tc_autotune(h, ctypes.byref(fields), float(dt), _stream_ptr(stream), ctypes.byref(c)), "tc_autotune")
+    return {"block": c.block, "blocks_per_sm": c.blocks_per_sm, "lanes_per_cell": c.lanes_per_cell, "ms": c.ms}
+
+
 def tc_step(h, fields: tc_fields, dt: float, stream=None) -> None:
     _check(lib.tc_step(h, ctypes.byref(fields), float(dt), _stream_ptr(stream)), "tc_step")
 
@@ -331,6 +347,9 @@ class Stepper:
     def step(self, d: dict, dt: float, stream=None, Zg: float = 1.0, Zd: float = 1.0) -> None:
         f = make_fields(d, Zg=Zg, Zd=Zd)
         tc_step(self.h, f, dt, stream)
+
+    def autotune(self, d: dict, dt: float, stream=None, Zg: float = 1.0, Zd: float = 1.0) -> dict:
+        return tc_autotune(self.h, make_fields(d, Zg=Zg, Zd=Zd), dt, stream)
 
     def step_host(self, cells: dict, dt: float, stream=None, Zg: float = 1.0, Zd: float = 1.0) -> None:
         tc_step_host(self.h, make_host_fields(cells, Zg=Zg, Zd=Zd), dt, stream)

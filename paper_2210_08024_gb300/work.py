@@ -15,6 +15,7 @@ scalar type; its counts per iteration are stated here from the code:
     mixed Newton iteration  45 add, 35 mul, 17 div   (its FP64 part)
     FP64 polish iteration   36 add, 31 mul, 13 div
     paper-scheme substep    18 add, 18 mul,  8 div   (FD slope, T update, 2x2 solve)
+    predictor sweep         30 add, 30 mul,  8 div   (2x2 closed form, T step, change)
 
     python -m paper_2210_08024_gb300.work
 """
@@ -41,6 +42,7 @@ LINALG = {
     "newton32_it": {"add": 45, "mul": 35, "div": 17},
     "polish_it": {"add": 36, "mul": 31, "div": 13},
     "substep_paper": {"add": 18, "mul": 18, "div": 8},
+    "picard_it": {"add": 30, "mul": 30, "div": 8},
 }
 CLASSES = ("add", "mul", "div", "sqrt", "exp", "log")
 BLOCKS = {"chem_T": "cost_chem_T", "cool_T": "cost_cool_T", "source": "cost_source", "equil": "cost_equil_setup",
@@ -56,20 +58,43 @@ def build(tmp: str) -> str:
     return exe
 
 
-def per_cell(counts: dict) -> dict:
-    """FP64 operations per cell by class for each mode."""
-    out = {}
-    for mode in ("mode0", "mode1", "mode2"):
-        calls = counts[mode]["fp64"]
-        tot = {c: 0.0 for c in CLASSES}
-        for blk, key in BLOCKS.items():
-            for c in CLASSES:
-                tot[c] += calls[blk] * counts[key][c]
+def _ops(calls: dict, counts: dict, linalg: bool) -> dict:
+    tot = {c: 0.0 for c in CLASSES}
+    for blk, key in BLOCKS.items():
+        for c in CLASSES:
+            tot[c] += calls.get(blk, 0.0) * counts[key][c]
+    if linalg:
         for blk, la in LINALG.items():
             for c, v in la.items():
-                tot[c] += calls[blk] * v
-        out[mode] = {c: round(v, 2) for c, v in tot.items()}
+                tot[c] += calls.get(blk, 0.0) * v
+    return {c: round(v, 2) for c, v in tot.items()}
+
+
+def per_cell(counts: dict) -> dict:
+    """FP64 operations per cell by class for each mode; for the mixed mode also its FP32
+    operations ("mode2_fp32": the same building blocks instantiated in FP32, whose
+    exp, log, sqrt and divide the fast-math build issues to the MUFU pipe)."""
+    out = {}
+    for mode in ("mode0", "mode1", "mode2"):
+        out[mode] = _ops(counts[mode]["fp64"], counts, True)
         out[mode]["substeps"] = counts[mode]["substeps"]
+    out["mode2_fp32"] = _ops(counts["mode2"]["fp32"], counts, False)
+    return out
+
+
+def algorithmic(counts: dict) -> dict:
+    """The method's own work knobs per slab cell: substeps, evaluations of the source
+    terms f (FP64 and FP32), and Newton-type iterations per substep."""
+    out = {}
+    for mode in ("mode0", "mode1", "mode2"):
+        k, f = counts[mode]["fp64"], counts[mode]["fp32"]
+        ns = counts[mode]["substeps"]
+        src = k["source"] + f["source"]
+        its = k["newton64_it"] + k["chord64_it"] + k["newton32_it"]
+        out[mode] = {"substeps": round(ns, 4), "source_evals": round(src, 3),
+                     "source_evals_per_substep": round(src / ns, 3) if ns else 0.0,
+                     "iterations_per_substep": round(its / ns, 3) if ns else 0.0,
+                     "fp64_polish_per_substep": round(k["polish_it"] / ns, 3) if ns else 0.0}
     return out
 
 
@@ -91,7 +116,7 @@ def main(sample: int = 8192):
     counts = json.loads(r.stdout)
     res = {"_comment": "FP64 operations per cell of one step (dt = 1e4 yr) on %d seeded cells of the 128^3 slab, "
                        "counted from the library's own step functions (paper_2210_08024_gb300/work.py)." % sample,
-           "per_cell": per_cell(counts), "raw": counts}
+           "per_cell": per_cell(counts), "algorithmic": algorithmic(counts), "raw": counts}
     with open(OUT, "w") as fh:
         json.dump(res, fh, indent=1)
     print(OUT)
