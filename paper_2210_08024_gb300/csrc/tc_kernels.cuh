@@ -236,27 +236,31 @@ TCG_FN void feval64(const CellC<double>& c, const ChemT<double>& b, const CoolT<
   f[2] = s.CHp;
 }
 
-TCG_FN bool solve3(double J[3][3], double b[3], double d[3]) {
+// Gaussian elimination with partial pivoting on a 3x3 system, in the precision F of its
+// operands (FP64 for the Newton steps of the FP64 solves; FP32 for the corrections of
+// the mixed solve, whose Jacobian is an FP32 forward difference good to ~1e-3 anyway).
+template <class F>
+TCG_FN bool solve3(F J[3][3], F b[3], F d[3]) {
   for (int kk = 0; kk < 3; ++kk) {
     int piv = kk;
-    double best = fabs(J[kk][kk]);
+    F best = m_abs(J[kk][kk]);
     for (int i = kk + 1; i < 3; ++i) {
-      double v = fabs(J[i][kk]);
+      F v = m_abs(J[i][kk]);
       if (v > best) { best = v; piv = i; }
     }
-    if (!(best > 0.0)) return false;
+    if (!(best > F(0))) return false;
     if (piv != kk) {
-      for (int j = 0; j < 3; ++j) { double tt = J[kk][j]; J[kk][j] = J[piv][j]; J[piv][j] = tt; }
-      double tb = b[kk]; b[kk] = b[piv]; b[piv] = tb;
+      for (int j = 0; j < 3; ++j) { F tt = J[kk][j]; J[kk][j] = J[piv][j]; J[piv][j] = tt; }
+      F tb = b[kk]; b[kk] = b[piv]; b[piv] = tb;
     }
     for (int i = kk + 1; i < 3; ++i) {
-      double m = J[i][kk] / J[kk][kk];
+      F m = J[i][kk] / J[kk][kk];
       for (int j = kk; j < 3; ++j) J[i][j] -= m * J[kk][j];
       b[i] -= m * b[kk];
     }
   }
   for (int i = 2; i >= 0; --i) {
-    double acc = b[i];
+    F acc = b[i];
     for (int j = i + 1; j < 3; ++j) acc -= J[i][j] * d[j];
     d[i] = acc / J[i][i];
   }
@@ -360,13 +364,14 @@ TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, do
       CoolT<double> k = cool_T(c, b, p.flags);
       feval64(c, b, k, y[1] + ((q == 1) ? h1 : 0.0), y[2] + ((q == 2) ? h2 : 0.0), Kinv, xg, tg, fq, &qq);
     }
+    const double s0 = dts / h0, s1 = dts / h1, s2 = dts / h2;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       f0[i] = from_lane<4>(fq[i], 0);
       const double f1 = from_lane<4>(fq[i], 1), f2 = from_lane<4>(fq[i], 2), fT = from_lane<4>(fq[i], 3);
-      J[i][1] = ((i == 1) ? 1.0 : 0.0) - dts * (f1 - f0[i]) / h1;
-      J[i][2] = ((i == 2) ? 1.0 : 0.0) - dts * (f2 - f0[i]) / h2;
-      J[i][0] = ((i == 0) ? 1.0 : 0.0) - dts * (fT - f0[i]) / h0;
+      J[i][1] = ((i == 1) ? 1.0 : 0.0) - s1 * (f1 - f0[i]);
+      J[i][2] = ((i == 2) ? 1.0 : 0.0) - s2 * (f2 - f0[i]);
+      J[i][0] = ((i == 0) ? 1.0 : 0.0) - s0 * (fT - f0[i]);
     }
     xe_g = from_lane<4>(xg, 0);
     td_g = from_lane<4>(tg, 0);
@@ -393,8 +398,8 @@ TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, do
     }
     feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, qb);
     for (int j = 1; j < 3; ++j) {
-      double h = fmax(1e-7 * fabs(y[j]), 1e-17);
-      for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - dts * (fx[j - 1][i] - f0[i]) / h;
+      const double sj = dts / fmax(1e-7 * fabs(y[j]), 1e-17);
+      for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - sj * (fx[j - 1][i] - f0[i]);
     }
     {
       double h = 1e-7 * y[0];
@@ -403,14 +408,15 @@ TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, do
       double xg = xe_g, tg = td_g;
       double fT[3];
       feval64(c, bT, kT, y[1], y[2], Kinv, xg, tg, fT);
-      for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - dts * (fT[i] - f0[i]) / h;
+      const double s0 = dts / h;
+      for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - s0 * (fT[i] - f0[i]);
     }
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) Jk[i][j] = J[i][j];
   }
   double rhs[3], d[3];
   for (int i = 0; i < 3; ++i) rhs[i] = -(y[i] - yn[i] - dts * f0[i]);
-  if (!solve3(J, rhs, d)) return -1;
+  if (!solve3<double>(J, rhs, d)) return -1;
   double st[3];
   full = damped_step(y, d, st);
   bool conv = full;
@@ -678,13 +684,14 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
         CoolT<float> k = cool_T(cf, b, p.flags);
         feval32(cf, b, k, y[1] + ((q == 1) ? h1 : 0.0), y[2] + ((q == 2) ? h2 : 0.0), Kinv, xg, tg, fq);
       }
+      const double s0 = dts / h0, s1 = dts / h1, s2 = dts / h2;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         f0[i] = from_lane<LPC>(fq[i], 0);
         const double f1 = from_lane<LPC>(fq[i], 1), f2 = from_lane<LPC>(fq[i], 2), fT = from_lane<LPC>(fq[i], 3);
-        J[i][1] = ((i == 1) ? 1.0 : 0.0) - dts * (f1 - f0[i]) / h1;
-        J[i][2] = ((i == 2) ? 1.0 : 0.0) - dts * (f2 - f0[i]) / h2;
-        J[i][0] = ((i == 0) ? 1.0 : 0.0) - dts * (fT - f0[i]) / h0;
+        J[i][1] = ((i == 1) ? 1.0 : 0.0) - s1 * (f1 - f0[i]);
+        J[i][2] = ((i == 2) ? 1.0 : 0.0) - s2 * (f2 - f0[i]);
+        J[i][0] = ((i == 0) ? 1.0 : 0.0) - s0 * (fT - f0[i]);
       }
       xe_g = from_lane<LPC>(xg, 0);
       td_g = from_lane<LPC>(tg, 0);
@@ -703,7 +710,8 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
         float xg = xe_g, tg = td_g;
         double fx[3];
         feval32(cf, b, k, y1, y2, Kinv, xg, tg, fx);
-        for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - dts * (fx[i] - f0[i]) / h;
+        const double sj = dts / h;
+        for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - sj * (fx[i] - f0[i]);
       }
       const double h = 1e-3 * y[0];
       ChemT<float> bT = chem_T(cf, float(mu * (y[0] + h)), p.flags);
@@ -711,16 +719,19 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
       float xg = xe_g, tg = td_g;
       double fT[3];
       feval32(cf, bT, kT, y[1], y[2], Kinv, xg, tg, fT);
-      for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - dts * (fT[i] - f0[i]) / h;
+      const double s0 = dts / h;
+      for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - s0 * (fT[i] - f0[i]);
       haveJ = true;
     }
     }
-    double Jw[3][3], rhs[3], d[3];
+    // residual in FP64 (a difference of nearby values), the correction solved in FP32
+    float Jw[3][3], rhs[3], d32[3];
     for (int i = 0; i < 3; ++i) {
-      rhs[i] = -(y[i] - yn[i] - dts * f0[i]);
-      for (int j = 0; j < 3; ++j) Jw[i][j] = J[i][j];
+      rhs[i] = float(-(y[i] - yn[i] - dts * f0[i]));
+      for (int j = 0; j < 3; ++j) Jw[i][j] = float(J[i][j]);
     }
-    if (!solve3(Jw, rhs, d)) return -1;
+    if (!solve3<float>(Jw, rhs, d32)) return -1;
+    const double d[3] = {double(d32[0]), double(d32[1]), double(d32[2])};
     double st[3];
     const bool full = damped_step(y, d, st);
     double nrm = 0.0;
@@ -770,12 +781,15 @@ TCG_FN bool polish64(const CellC<double>& c, const DevParams& p, double mu, doub
     CoolT<double> k = cool_T(c, b, p.flags);
     double f0[3];
     feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, &qlast);
-    double Jw[3][3], rhs[3], d[3];
+    // FP64 residual; the correction (below ~1e-6 relative) solved in FP32 with the FP32
+    // Jacobian, whose own error (~1e-3) sets the contraction
+    float Jw[3][3], rhs[3], d32[3];
     for (int i = 0; i < 3; ++i) {
-      rhs[i] = -(y[i] - yn[i] - dts * f0[i]);
-      for (int j = 0; j < 3; ++j) Jw[i][j] = J[i][j];
+      rhs[i] = float(-(y[i] - yn[i] - dts * f0[i]));
+      for (int j = 0; j < 3; ++j) Jw[i][j] = float(J[i][j]);
     }
-    if (!solve3(Jw, rhs, d)) return false;
+    if (!solve3<float>(Jw, rhs, d32)) return false;
+    const double d[3] = {double(d32[0]), double(d32[1]), double(d32[2])};
     double st[3];
     const bool full = damped_step(y, d, st);
     double nrm = 0.0;

@@ -9,11 +9,12 @@ each class, measured in the same run, to state the work one launch performs.
 The dense 3x3 linear algebra of each Newton iteration (FD-Jacobian differencing, the
 residual, Gaussian elimination, damping and convergence test) is not templated on the
 scalar type; its counts per iteration are stated here from the code:
-    FP64 Newton iteration   63 add, 55 mul, 22 div
+    FP64 Newton iteration   63 add, 55 mul, 16 div   (one division per Jacobian column)
     FP64 chord iteration    42 add, 40 mul, 13 div   (the same without the differencing:
                                                       21 add, 15 mul, 9 div)
-    mixed Newton iteration  45 add, 35 mul, 17 div   (its FP64 part)
-    FP64 polish iteration   36 add, 31 mul, 13 div
+    mixed Newton iteration  18 add, 12 mul,  6 div   (its FP64 part: residual, damped step
+                                                      and test; the correction is solved in FP32)
+    FP64 polish iteration   16 add, 12 mul,  6 div   (the same with the FP64 residual)
     paper-scheme substep    18 add, 18 mul,  8 div   (FD slope, T update, 2x2 solve)
     predictor sweep         30 add, 30 mul,  8 div   (2x2 closed form, T step, change)
 
@@ -37,10 +38,10 @@ if ROOT not in sys.path:
 
 OUT = os.path.join(HERE, "work_slab128.json")
 LINALG = {
-    "newton64_it": {"add": 63, "mul": 55, "div": 22},
+    "newton64_it": {"add": 63, "mul": 55, "div": 16},
     "chord64_it": {"add": 42, "mul": 40, "div": 13},
-    "newton32_it": {"add": 45, "mul": 35, "div": 17},
-    "polish_it": {"add": 36, "mul": 31, "div": 13},
+    "newton32_it": {"add": 18, "mul": 12, "div": 6},
+    "polish_it": {"add": 16, "mul": 12, "div": 6},
     "substep_paper": {"add": 18, "mul": 18, "div": 8},
     "picard_it": {"add": 30, "mul": 30, "div": 8},
 }
