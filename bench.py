@@ -284,6 +284,10 @@ def run_gpu(args):
                           "value": job_throughput(ncell, ws, args.steps, ms), "launches": launches,
                           "cells_not_ok": nbad, "newton_iters_per_cell": float(dev["iters"].double().mean().item()),
                           "launch_shape": shape, "mode_id": mode_ids[mname]}
+        if "seeded" in mname:
+            stt = dev["status"]
+            results[mname]["cells_with_a_seeded_solve"] = float(((stt & tc.TC_ST_SEEDED) != 0).double().mean().item())
+            results[mname]["cells_with_a_failed_seed"] = float(((stt & tc.TC_ST_SEED_FAIL) != 0).double().mean().item())
         st.close()
 
     head = modes[0]

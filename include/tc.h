@@ -60,6 +60,9 @@ extern "C" {
 #define TC_ST_POLISHED 16    /* a mixed solve stopped at the FP32 rounding floor before its FP64 polish */
 #define TC_ST_PREDICTOR 32   /* a Newton solve from the start state failed and was restarted from the
                                  block predictor (abundances by the 2x2 backward Euler, then T) */
+#define TC_ST_SEEDED 64      /* seeded modes: a substep's solve started from the seed network converged */
+#define TC_ST_SEED_FAIL 128  /* seeded modes: a seeded solve did not converge in 6 iterations and the
+                                substep restarted from its start state (those iterations are counted) */
 #define TC_ST_ERROR_MASK 7
 
 typedef struct tc_params {
@@ -116,7 +119,8 @@ typedef struct tc_fields {
   long long ncell;
   double Zg_val, Zd_val;    /* scalars used when Zg / Zd are NULL */
   int *newton_iters;        /* optional out (device, may be NULL): Newton iterations summed over the
-                               cell's substeps (modes 1-4; the mixed modes count FP32 iterations) */
+                               cell's substeps (modes 1-4; the mixed modes count FP32 iterations;
+                               the seeded modes include abandoned seeded attempts) */
   const int *cost_hint;     /* optional in (device, may be NULL; tc_step and tc_step_batch only): a
                                per-cell cost estimate, larger = costlier, for example the newton_iters
                                output of the cell's previous step.  With tc_params.order_cells set,
@@ -149,6 +153,17 @@ int tc_step(tc_handle *h, const tc_fields *f, double dt_s, void *stream);
  * descriptors (1 <= nbox <= 64), read before the call returns.  Returns TC_EINVAL for a
  * bad count or descriptor, TC_ECUDA if capture or launch fails. */
 int tc_step_batch(tc_handle *h, const tc_fields *boxes, int nbox, double dt_s, void *stream);
+
+/* Start-state source terms of the substep rule (Sec. 6.1, with Eqs. e:ODE1, e:HH,
+ * e:HII): for every cell of *f (device pointers as for tc_step; its state is only read)
+ * the step's own start -- the C/O/e equilibrium at the input T, mu, T_mu -- and then
+ * rate[3 i + 0] = C_H2, rate[3 i + 1] = C_H+ (the rates of change of x_H2 and x_H+,
+ * s^-1) and rate[3 i + 2] = H / (K T_mu) (that of ln T_mu, s^-1), all FP64, and
+ * dts[i] = the length in seconds of the first substep of a step of dt_s.  rate (3 ncell
+ * doubles) and dts (ncell doubles) are device arrays; either may be NULL.  Enqueued on
+ * `stream`.  These are the explicit-Euler rates that the seed network takes as inputs
+ * (tc_mlp.h).  Returns TC_EINVAL for bad fields or dt_s, TC_ECUDA if the launch fails. */
+int tc_rates(tc_handle *h, const tc_fields *f, double dt_s, double *rate, double *dts, void *stream);
 
 /* Launch shape chosen by tc_autotune (the library's scheduling; the paper has no
  * counterpart). */

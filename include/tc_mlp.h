@@ -8,14 +8,17 @@
  * learned component: this is the build's acceleration of its coupled implicit scheme
  * (Sec. 6.1).
  *
- * Network: 10 features -> 64 -> 64 -> 64 (SiLU) -> 3 outputs.
+ * Network: 13 features -> 64 -> 64 -> 64 (SiLU) -> 3 outputs.
  *   features: log10 n, log10 T, x_H2, x_H+, log10 chi_FUV, log10 f_shld,H2,
- *             log10(F_LyC + 1), log10 xi_cr, log10 dt   (raw; normalised inside with the
- *             mean and standard deviation given to tc_mlp_set_norm)
+ *             log10(F_LyC + 1), log10 xi_cr, log10 dt, log10 Z'_d, and the explicit-Euler
+ *             changes over the step g = dt (C_H2 / 0.5, C_H+, H / (K T_mu ln 10)) from the
+ *             start-state source terms (tc_rates in tc.h)   (raw; normalised inside with
+ *             the mean and standard deviation given to tc_mlp_set_norm)
  *   outputs:  changes over one backward-Euler step of length dt (the implicit solve's
- *             root): (x_H2' - x_H2)/0.5, x_H+' - x_H+, log10 T' - log10 T
+ *             root) minus g: (x_H2' - x_H2)/0.5 - g0, x_H+' - x_H+ - g1,
+ *             log10 T' - log10 T - g2
  * Parameters: one FP32 master vector of tc_mlp_n_params() floats, in the order
- *   W1[64][10], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[3][64], b4[3].
+ *   W1[64][13], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[3][64], b4[3].
  * The forward and backward passes use the weights rounded to BF16 and accumulate in
  * FP32.  Training is Adam on the FP32 masters.
  *
@@ -34,7 +37,7 @@ extern "C" {
 
 typedef struct tc_mlp tc_mlp;
 
-/* Number of FP32 parameters (9219). */
+/* Number of FP32 parameters (9411). */
 int tc_mlp_n_params(void);
 
 /* Creates a network on the current device: uniform initialisation with bound
@@ -50,7 +53,7 @@ int tc_mlp_set_norm(tc_mlp *h, const float *mean, const float *stdev);
 int tc_mlp_set_params(tc_mlp *h, const float *theta);
 int tc_mlp_get_params(const tc_mlp *h, float *theta);
 
-/* out[B][3] = network(X[B][10]) on `stream`. */
+/* out[B][3] = network(X[B][13]) on `stream`. */
 int tc_mlp_predict(tc_mlp *h, const float *X, int B, float *out, void *stream);
 
 /* Gradient of the weighted mean-squared error sum_m w_m (o_m - y_m)^2 / B with respect

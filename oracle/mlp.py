@@ -8,8 +8,8 @@ analytic backward pass.  The CUDA training kernels are checked against it; it sh
 no code with them.
 
 Layout (the same conventions as the library's blob):
-    inputs   x[B, 10]  (already normalised)
-    layer l  h_l = silu(h_{l-1} W_l^T + b_l),  W_1: [64, 10], W_2, W_3: [64, 64]
+    inputs   x[B, 13]  (already normalised)
+    layer l  h_l = silu(h_{l-1} W_l^T + b_l),  W_1: [64, 13], W_2, W_3: [64, 64]
     output   o = h_3 W_4^T + b_4,  W_4: [3, 64]
     loss     L = sum_b sum_j w_j (o_bj - y_bj)^2 / B
 silu(z) = z / (1 + exp(-z)).
@@ -18,7 +18,7 @@ from __future__ import annotations
 
 import numpy as np
 
-N_IN, N_HID, N_OUT = 10, 64, 3
+N_IN, N_HID, N_OUT = 13, 64, 3
 SHAPES = [(N_HID, N_IN), (N_HID,), (N_HID, N_HID), (N_HID,), (N_HID, N_HID), (N_HID,), (N_OUT, N_HID), (N_OUT,)]
 
 

@@ -336,6 +336,19 @@ int tc_step(tc_handle* h, const tc_fields* f, double dt_s, void* stream) {
   return enqueue(h, false, dev_fields(f), f->ncell, dt_s, (cudaStream_t)stream);
 }
 
+int tc_rates(tc_handle* h, const tc_fields* f, double dt_s, double* rate, double* dts, void* stream) {
+  if (!h) return TC_EINVAL;
+  int rc = check_fields(f);
+  if (rc != TC_OK) return rc;
+  if (!(dt_s >= 0.0) || !isfinite(dt_s)) return TC_EINVAL;
+  if (f->ncell == 0 || (!rate && !dts)) return TC_OK;
+  if (tcg::launch_rates(dev_fields(f), dev_params(h->p), dt_s, f->ncell, rate, dts, h->num_sms,
+                        (cudaStream_t)stream) != cudaSuccess)
+    return TC_ECUDA;
+  h->launches += 1;
+  return TC_OK;
+}
+
 int tc_autotune(tc_handle* h, const tc_fields* f, double dt_s, void* stream, tc_tune_choice* best) {
   if (!h || !best) return TC_EINVAL;
   int rc = check_fields(f);

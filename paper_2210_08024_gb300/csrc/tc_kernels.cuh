@@ -42,6 +42,10 @@ struct BoxTable {
 };
 
 constexpr int ST_MAX_SUB = 1, ST_NEWTON = 2, ST_NONFIN = 4, ST_FALLBACK = 8, ST_POLISH = 16, ST_PREDICTOR = 32;
+// seeded modes (informational): a substep's solve started from the seed network's
+// prediction converged (ST_SEEDED), or failed and restarted from the start state
+// (ST_SEED_FAIL)
+constexpr int ST_SEEDED = 64, ST_SEED_FAIL = 128;
 
 __device__ __forceinline__ long long claim_cells(unsigned long long* cursor) {
   unsigned mask = __activemask();
@@ -436,7 +440,7 @@ TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, do
 template <int LPC = 1>
 TCG_FN int newton_solve(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
                         double dts, double* y, double& xe_g, double& td_g, int maxit = 0,
-                        Equil<double>* qb = nullptr) {
+                        Equil<double>* qb = nullptr, int* spent = nullptr) {
   const int nmax = (maxit > 0 && maxit < p.newton_max) ? maxit : p.newton_max;
   double Jk[3][3];
   bool reuse = false;
@@ -445,6 +449,7 @@ TCG_FN int newton_solve(const CellC<double>& c, const DevParams& p, double mu, d
     double rel;
     bool full;
     const int r = newton_iter<LPC>(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, Jk, reuse, rel, full, qb);
+    if (spent) *spent = it;
     if (r < 0) return -1;
     if (r > 0) return it;
     reuse = full && rel < JAC_REUSE && (!reuse || rel <= 0.5 * prev);
@@ -598,8 +603,15 @@ TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double d
   if (seed) {
     y[0] = seed[0]; y[1] = seed[1]; y[2] = seed[2];
     double xg = xe_g, tg = td_g;
-    it = newton_solve<LPC>(c, p, s.mu, Kinv, yn, dts, y, xg, tg, SEED_MAXIT, &qb);
-    if (it >= 0) { xe_g = xg; td_g = tg; }
+    int spent = 0;
+    it = newton_solve<LPC>(c, p, s.mu, Kinv, yn, dts, y, xg, tg, SEED_MAXIT, &qb, &spent);
+    if (it >= 0) {
+      xe_g = xg; td_g = tg;
+      s.status |= ST_SEEDED;
+    } else {
+      s.iters += spent;   // the abandoned seeded iterations count too
+      s.status |= ST_SEED_FAIL;
+    }
   }
   if (it < 0) it = solve_from_start64<LPC>(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status, &qb);
   int halv = 0;
@@ -619,11 +631,13 @@ TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double d
   finish_substep_q(c, p, dt, dts, last, y, qb, s);
 }
 
-// Substep length of Sec. 6.1 from the FP64 source terms at the substep start.
+// Substep length of Sec. 6.1 from the FP64 source terms at the substep start; `src`,
+// when given, receives those terms (H, C_H2, C_H+).
 TCG_FN double substep_start64(const CellC<double>& c, const DevParams& p, double dt, const LaneState& s,
-                              double& td_g, bool& last) {
+                              double& td_g, bool& last, double* src = nullptr) {
   double H0, CH2, CHp;
   start_sources<double>(c, p, s, td_g, H0, CH2, CHp);
+  if (src) { src[0] = H0; src[1] = CH2; src[2] = CHp; }
   return substep_len(p, dt - s.t, c.K * s.Tmu, H0, CH2, CHp, last);
 }
 
@@ -662,12 +676,15 @@ TCG_FN void feval32(const CellC<float>& cf, const ChemT<float>& b, const CoolT<f
 // of large terms; or -1 if neither happened.  J holds the last Jacobian on return.
 template <int LPC = 1>
 TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, double Kinv, const double* yn,
-                        double dts, double* y, float& xe_g, float& td_g, double J[3][3], bool& polish) {
+                        double dts, double* y, float& xe_g, float& td_g, double J[3][3], bool& polish,
+                        int maxit = 0, int* spent = nullptr) {
   bool haveJ = false;
   int rebuilt = 0;
   double prev = 1e300;
   polish = false;
-  for (int it = 1; it <= p.newton_max; ++it) {
+  const int nmax = (maxit > 0 && maxit < p.newton_max) ? maxit : p.newton_max;
+  for (int it = 1; it <= nmax; ++it) {
+    if (spent) *spent = it;
     TCG_COUNT_D(newton32_it);
     double f0[3];
     bool coop = false;
@@ -827,9 +844,13 @@ TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<float>& cf, 
   if (seed) { y[0] = seed[0]; y[1] = seed[1]; y[2] = seed[2]; }
   double J[3][3];
   bool polish = false;
-  int it = newton_mixed<LPC>(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, J, polish);
+  int spent = 0;
+  int it = newton_mixed<LPC>(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, J, polish, seed ? SEED_MAXIT : 0, &spent);
+  if (seed) s.status |= (it >= 0) ? ST_SEEDED : ST_SEED_FAIL;
   if (it < 0 && seed) {
-    // a seed that did not lead to convergence: start again from the start state
+    // a seed that did not lead to convergence within SEED_MAXIT iterations: start again
+    // from the start state (the abandoned iterations count too)
+    s.iters += spent;
     y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2];
     it = newton_mixed<LPC>(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, J, polish);
   }
@@ -864,29 +885,33 @@ TCG_FN void substep_mixed(const CellC<double>& c, const CellC<float>& cf, const 
 // accuracy): 256 bytes of per-thread local memory instead of 512.
 using seed_act_t = __half;
 
-// Seed of a substep's Newton iteration from the network: features of the substep start
-// (state, per-cell features lf[6] = log10 n, log10 chi_FUV, log10 f_shld,H2,
-// log10(F_LyC+1), log10 xi, log10 Z'_d) and its length; the outputs are the predicted changes of
-// x_H2 (/0.5), x_H+ and log10 T over the substep's backward-Euler step, mapped to
-// (T_mu, x_H2, x_H+) with mu frozen at the substep start and clamped inside the
-// admissible region.  Returns
-// false (no seed) if the prediction is not finite.
+// Seed of a substep's Newton iteration from the network.  Features: the substep start's
+// state, the per-cell features lf[6] = log10 n, log10 chi_FUV, log10 f_shld,H2,
+// log10(F_LyC+1), log10 xi, log10 Z'_d, the substep length, and the explicit-Euler
+// changes over the substep from the start-state source terms src = (H, C_H2, C_H+)
+// that set its length: g = dts (C_H2 / 0.5, C_H+, H / (K T_mu ln 10)).  The outputs are
+// the backward-Euler changes of x_H2 (/0.5), x_H+ and log10 T minus those explicit
+// ones, so the prediction is g + output; it is mapped to (T_mu, x_H2, x_H+) with mu
+// frozen at the substep start and clamped inside the admissible region.  Returns false
+// (no seed) if the prediction is not finite or leaves the trust region below.
 TCG_FN bool mlp_seed(const MlpDev* __restrict__ w, seed_act_t* buf0, seed_act_t* buf1, int st, const float* lf,
-                     const LaneState& s,
-                     double dts, const DevParams& p, double* seed) {
+                     const CellC<double>& c, const LaneState& s, double dts, const double* src, const DevParams& p,
+                     double* seed) {
   const double T0 = s.mu * s.Tmu;
+  const double g0 = dts * src[1] / 0.5, g1 = dts * src[2], g2 = dts * src[0] / (c.K * s.Tmu) / LN10;
   float f[MLP_IN] = {lf[0], (float)log10(T0), (float)s.xH2, (float)s.xHp, lf[1], lf[2], lf[3], lf[4],
-                     (float)log10(dts), lf[5]};
+                     (float)log10(dts), lf[5], (float)g0, (float)g1, (float)g2};
   float o[MLP_OUT];
   mlp_infer(w, buf0, buf1, st, f, o);
-  if (!(isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]))) return false;
+  const double d0 = g0 + (double)o[0], d1 = g1 + (double)o[1], d2 = g2 + (double)o[2];
+  if (!(isfinite(d0) && isfinite(d1) && isfinite(d2))) return false;
   // Trust region: the backward-Euler system can have several roots (thermally unstable
   // gas), and the solver's root is the one Newton reaches from the start state.  A seed
   // is used only when it predicts a small change, inside the basin of that root.
-  if (fabsf(o[2]) > SEED_MAX_DLOGT || fabsf(0.5f * o[0]) > SEED_MAX_DX || fabsf(o[1]) > SEED_MAX_DX) return false;
-  const double x2 = fmin(fmax(s.xH2 + 0.5 * (double)o[0], 1e-20), 0.4999999);
-  const double xp = fmin(fmax(s.xHp + (double)o[1], 1e-20), 0.999999 * (1.0 - 2.0 * x2));
-  const double T1 = fmin(fmax(T0 * exp10((double)fmin(fmax(o[2], -6.f), 6.f)), p.T_floor), 1e10);
+  if (fabs(d2) > SEED_MAX_DLOGT || fabs(0.5 * d0) > SEED_MAX_DX || fabs(d1) > SEED_MAX_DX) return false;
+  const double x2 = fmin(fmax(s.xH2 + 0.5 * d0, 1e-20), 0.4999999);
+  const double xp = fmin(fmax(s.xHp + d1, 1e-20), 0.999999 * (1.0 - 2.0 * x2));
+  const double T1 = fmin(fmax(T0 * exp10(fmin(fmax(d2, -6.0), 6.0)), p.T_floor), 1e10);
   seed[0] = T1 / s.mu;
   seed[1] = x2;
   seed[2] = xp;
@@ -1003,9 +1028,10 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
         substep_mixed<LPC>(c, cf, p, dt, s, xe_gf, td_gf, td64);
       } else {
         bool last;
-        const double dts = substep_start64(c, p, dt, s, (MODE == 3) ? td64 : td_g, last);
+        double src[3];
+        const double dts = substep_start64(c, p, dt, s, (MODE == 3) ? td64 : td_g, last, src);
         double seed[3];
-        const bool ok = mlp_seed(wsm, buf0, buf1, 1, lf, s, dts, p, seed);
+        const bool ok = mlp_seed(wsm, buf0, buf1, 1, lf, c, s, dts, src, p, seed);
         if constexpr (MODE == 3) substep_mixed_solve(c, cf, p, dt, dts, last, s, xe_gf, td_gf, td64, ok ? seed : nullptr);
         else solve_substep64(c, p, dt, dts, last, s, xe_g, td_g, ok ? seed : nullptr);
       }

@@ -1,7 +1,7 @@
 // Training of the seed network on the GPU (declared in include/tc_mlp.h).
 //
 // Parameters live on the device as one FP32 master vector in the order
-//   W1[64][10], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[3][64], b4[3]
+//   W1[64][13], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[3][64], b4[3]
 // (weights [out][in]).  The forward and backward passes use the weights rounded to
 // BF16, as the step kernel's inference does, and accumulate in FP32.  The weight
 // gradient of the BF16 network is applied to the FP32 masters by Adam.

@@ -1,13 +1,14 @@
 // Seed network of the implicit solve: layout of its weights on the device and the
 // per-lane inference used inside the step kernel.
 //
-// The network maps a cell's state, fields, metallicity and step length (10 features)
-// through three
-// hidden layers of 64 SiLU units to 3 outputs, the changes over one backward-Euler
-// step of length dt (the root the implicit solve looks for):
-//   o0 ~ (x_H2' - x_H2) / 0.5,  o1 ~ x_H+' - x_H+,  o2 ~ log10 T' - log10 T.
+// The network maps a cell's state, fields, metallicity, step length and the
+// explicit-Euler changes over the step (13 features) through three hidden layers of 64
+// SiLU units to 3 outputs: the changes over one backward-Euler step of length dt (the
+// root the implicit solve looks for) minus the explicit-Euler ones,
+//   o0 ~ (x_H2' - x_H2) / 0.5 - g0,  o1 ~ x_H+' - x_H+ - g1,  o2 ~ log10 T' - log10 T - g2,
+// with g = dt (C_H2 / 0.5, C_H+, H / (K T_mu ln 10)) from the source terms at the start.
 // Features: log10 n, log10 T, x_H2, x_H+, log10 chi_FUV, log10 f_shld,H2,
-// log10(F_LyC + 1), log10 xi_cr, log10 dt, log10 Z'_d; each normalised as
+// log10(F_LyC + 1), log10 xi_cr, log10 dt, log10 Z'_d, g0, g1, g2; each normalised as
 // (f - mean) * inv_std.
 // Weights are BF16, everything else FP32; sums accumulate in FP32.
 #pragma once
@@ -19,10 +20,10 @@
 
 namespace tcg {
 
-constexpr int MLP_IN = 10, MLP_HID = 64, MLP_OUT = 3;
+constexpr int MLP_IN = 13, MLP_HID = 64, MLP_OUT = 3;
 constexpr int MLP_INP = 16;   // padded input width of W1
 constexpr uint32_t MLP_MAGIC = 0x4C4D4354u;  // "TCML"
-constexpr uint32_t MLP_VERSION = 2u;   // 2: ten inputs (Z'_d added)
+constexpr uint32_t MLP_VERSION = 3u;   // 3: thirteen inputs (explicit-Euler changes added)
 
 // Weights are stored transposed ([in][out]) so that one input's weights for 16
 // consecutive outputs are contiguous (two 16-byte loads, broadcast to the warp).
@@ -30,7 +31,7 @@ struct MlpDev {
   uint32_t magic, version, n_in, n_hid, n_out, bytes, pad0, pad1;
   float in_mean[MLP_INP];
   float in_inv_std[MLP_INP];
-  __nv_bfloat16 W1t[MLP_INP * MLP_HID];   // [k][j], rows k >= 10 zero
+  __nv_bfloat16 W1t[MLP_INP * MLP_HID];   // [k][j], rows k >= MLP_IN zero
   __nv_bfloat16 W2t[MLP_HID * MLP_HID];   // [k][j]
   __nv_bfloat16 W3t[MLP_HID * MLP_HID];   // [k][j]
   __nv_bfloat16 W4t[MLP_HID * 4];         // [k][m], column 3 zero
@@ -82,7 +83,7 @@ TCG_MLP_FN void mlp_layer(const __nv_bfloat16* __restrict__ Wt, const float* __r
   }
 }
 
-// Network output for raw features f[10].  `w` points to the weights; buf0/buf1 point
+// Network output for raw features f[MLP_IN].  `w` points to the weights; buf0/buf1 point
 // to this thread's two activation buffers of 64 entries at stride `st`.
 template <class A>
 TCG_MLP_FN void mlp_infer(const MlpDev* w, A* buf0, A* buf1, int st, const float* f, float* o) {

@@ -137,7 +137,51 @@ __global__ void __launch_bounds__(256) k_order_scatter(const unsigned char* __re
   }
 }
 
+// One thread per cell: the step's prologue (initial C/O/e equilibrium, mu, T_mu) and
+// its start-state sources in FP64, as the step kernel computes them.
+__global__ void __launch_bounds__(128) k_rates(DevFields f, DevParams p, double dt, long long ntotal,
+                                               double* __restrict__ rate, double* __restrict__ dts) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ntotal;
+       i += (long long)gridDim.x * blockDim.x) {
+    CellC<double> c;
+    double T0, x20, xp0;
+    load_cell(f, i, p, c, T0, x20, xp0);
+    LaneState s;
+    s.t = 0.0;
+    s.xH2 = x20;
+    s.xHp = xp0;
+    ChemT<double> b0 = chem_T(c, T0, p.flags);
+    Equil<double> q0 = equilibrium(c, b0, x20, xp0, -1.0);
+    s.xe = q0.xe; s.xCp = q0.xCp; s.xCO = q0.xCO;
+    s.mu = c.muH / (1.1 + s.xe - x20);
+    s.Tmu = T0 / s.mu;
+    double td = -1.0, H0, CH2, CHp;
+    start_sources<double>(c, p, s, td, H0, CH2, CHp);
+    if (rate) {
+      rate[3 * i + 0] = CH2;
+      rate[3 * i + 1] = CHp;
+      rate[3 * i + 2] = H0 / (c.K * s.Tmu);
+    }
+    if (dts) {
+      bool last;
+      dts[i] = substep_len(p, dt, c.K * s.Tmu, H0, CH2, CHp, last);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_rates(const DevFields& f, const DevParams& p, double dt, long long ntotal, double* rate,
+                         double* dts, int num_sms, cudaStream_t st) {
+  long long nb = (ntotal + 127) / 128;
+  const long long cap = (long long)num_sms * 8;
+  if (nb > cap) nb = cap;
+  if (nb < 1) nb = 1;
+  DevParams q = p;
+  q.order = nullptr;
+  k_rates<<<(int)nb, 128, 0, st>>>(f, q, dt, ntotal, rate, dts);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_order(bool batch, const DevFields& f, const BoxTable* d_boxes, const DevParams& p, double dt,
                          long long ntotal, unsigned char* key, unsigned* hist, unsigned* order, int num_sms,

@@ -17,4 +17,10 @@ cudaError_t launch_order(bool batch, const DevFields& f, const BoxTable* d_boxes
                          long long ntotal, unsigned char* key, unsigned* hist, unsigned* order, int num_sms,
                          cudaStream_t st);
 
+// Start-state source terms of the substep rule of Sec. 6.1 for every cell (tc_rates):
+// rate[3 i + 0..2] = (C_H2, C_H+, H / (K T_mu)) and dts[i] = the first substep length of
+// a step of dt; either output may be null.
+cudaError_t launch_rates(const DevFields& f, const DevParams& p, double dt, long long ntotal, double* rate,
+                         double* dts, int num_sms, cudaStream_t st);
+
 }  // namespace tcg

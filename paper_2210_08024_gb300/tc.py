@@ -16,6 +16,7 @@ TC_OK, TC_EINVAL, TC_ECUDA, TC_ENOMEM, TC_ENOMLP, TC_ENODEV = 0, -1, -2, -3, -4,
 TC_MODE_PAPER_FP64, TC_MODE_NEWTON_FP64, TC_MODE_MIXED, TC_MODE_MIXED_SEEDED, TC_MODE_NEWTON_FP64_SEEDED = 0, 1, 2, 3, 4
 TC_CONST_KGR, TC_NO_ROVIB, TC_NO_CIE = 1, 2, 4
 TC_ST_MAX_SUBSTEPS, TC_ST_NEWTON, TC_ST_NONFINITE, TC_ST_FALLBACK, TC_ST_POLISHED, TC_ST_PREDICTOR = 1, 2, 4, 8, 16, 32
+TC_ST_SEEDED, TC_ST_SEED_FAIL = 64, 128
 TC_ST_ERROR_MASK = 7
 
 
@@ -120,6 +121,8 @@ def _load():
     L.tc_create.argtypes = [ctypes.POINTER(tc_params), ctypes.POINTER(ctypes.c_void_p)]
     L.tc_step.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_double, ctypes.c_void_p]
     L.tc_step_host.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_double, ctypes.c_void_p]
+    L.tc_rates.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_double, ctypes.c_void_p,
+                           ctypes.c_void_p, ctypes.c_void_p]
     L.tc_autotune.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_double, ctypes.c_void_p,
                               ctypes.POINTER(tc_tune_choice)]
     L.tc_step_batch.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_int, ctypes.c_double,
@@ -195,6 +198,10 @@ def tc_destroy(h) -> None:
     lib.tc_destroy(h)
 
 
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
 def _stream_ptr(stream):
     if stream is None:
         import torch
@@ -245,6 +252,13 @@ def make_host_fields(arrs: dict, Zg: float = 1.0, Zd: float = 1.0) -> tc_fields:
     f.Zg_val = float(Zg)
     f.Zd_val = float(Zd)
     return f
+
+
+def tc_rates(h, fields: tc_fields, dt: float, rate=None, dts=None, stream=None) -> None:
+    """Start-state source terms (C_H2, C_H+, H/(K T_mu)) into `rate` (device float64,
+    3 per cell) and the first substep length of a step of dt into `dts` (device
+    float64), either may be None."""
+    _check(lib.tc_rates(h, ctypes.byref(fields), float(dt), _ptr(rate), _ptr(dts), _stream_ptr(stream)), "tc_rates")
 
 
 def tc_autotune(h, fields: tc_fields, dt: float, stream=None) -> dict:

@@ -142,12 +142,33 @@ def _run(tc, cells, mode, blob=None):
     return out
 
 
+def test_training_labels_match_oracle(tc):
+    # The seed network's labels are single backward-Euler roots from the library's FP64
+    # solver with the substep limiter off; 10k of them re-checked against the CPU
+    # oracle's coupled scheme at the FP64 bound, over step lengths 1e4 .. 1e11 s.
+    from paper_2210_08024_gb300 import seed_net
+    n = 10000
+    cells = synthgen.training_samples(n, key=45)
+    cells.pop("dt")
+    b = np.random.default_rng(3).integers(80, 221, n)
+    ok = np.ones(n, dtype=bool)
+    lab = seed_net.label_states(cells, b, 20, ok)
+    p = oracle.default_params(mode=1, limiter=1e30)
+    for bk in np.unique(b):
+        idx = np.nonzero(b == bk)[0]
+        ref = oracle.step(synthgen.subset(cells, idx), 10.0 ** (bk / 20), p)
+        assert np.array_equal(lab["nsub"][idx], ref["nsub"])
+        assert_fp64_parity({k: lab[k][idx] for k in ("T", "xH2", "xHp")}, ref, "labels dt=%g" % 10.0 ** (bk / 20))
+
+
 @pytest.mark.parametrize("workload", ["slab", "random"])
 def test_seeded_fp64_same_root_and_iteration_count(tc, trained_blob, workload):
-    # The seeded solve must reach the same root as the unseeded one; what the network
-    # gains is reported as Newton iterations per cell (printed with -s).  The gain is
-    # small: with the 0.1 substep limiter the start state is already within ~10% of the
-    # root, and Newton converges quadratically from there.
+    # The seeded solve must reach the same root as the unseeded one, and on the slab
+    # (the network's training distribution) it must need fewer Newton-type iterations:
+    # the network predicts each substep's root from the explicit-Euler changes and the
+    # state, and Newton starts there instead of at the start state.  The random states
+    # lie outside that distribution (up to 1e7 K): there the trust region keeps most
+    # seeds out and the count may not fall.
     c = synthgen.slab(ncell=20000, key=41) if workload == "slab" else synthgen.cells_4096(n=2048, key=43)
     plain = _run(tc, c, tc.TC_MODE_NEWTON_FP64)
     seeded = _run(tc, c, tc.TC_MODE_NEWTON_FP64_SEEDED, trained_blob)
@@ -157,7 +178,10 @@ def test_seeded_fp64_same_root_and_iteration_count(tc, trained_blob, workload):
     assert_fp64_parity(synthgen.subset(seeded, slice(0, 2000)), ref, "seeded-vs-oracle")
     print("%s: Newton iterations per cell: plain %.3f, seeded %.3f" % (workload, plain["iters"].mean(),
                                                                         seeded["iters"].mean()))
-    assert seeded["iters"].sum() <= 1.1 * plain["iters"].sum()
+    if workload == "slab":
+        assert seeded["iters"].sum() <= 0.85 * plain["iters"].sum()
+    else:
+        assert seeded["iters"].sum() <= 1.05 * plain["iters"].sum()
 
 
 def test_seeded_mixed_within_tolerance(tc, trained_blob):

@@ -17,7 +17,7 @@ def _rand(seed=0, B=7):
 
 
 def test_param_count_and_layout():
-    assert mlp.n_params() == 64 * 10 + 64 + 2 * (64 * 64 + 64) + 3 * 64 + 3
+    assert mlp.n_params() == 64 * 13 + 64 + 2 * (64 * 64 + 64) + 3 * 64 + 3
     theta, _, _ = _rand()
     assert np.array_equal(mlp.flatten(mlp.unflatten(theta)), theta)
 
