@@ -248,7 +248,8 @@ def run_gpu(args):
             st.load_mlp(blob)
         f = tc.make_fields(dev)
         # launch shape: the library's autotuner times its candidates on this workload
-        # (on a scratch copy of the state) before the timed region
+        # (on a scratch copy of the initial state) before the timed region
+        restore()
         shape = tc.tc_autotune(st.h, f, DT, stream)
         for _ in range(args.warmup):
             restore()
