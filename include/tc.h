@@ -222,6 +222,15 @@ int tc_step_host_static(const tc_params *p, const tc_fields *f, double dt_s, voi
  * size or layout version.  Required before a step in a seeded mode. */
 int tc_load_mlp(tc_handle *h, const void *blob, size_t bytes);
 
+/* The seed network as the seeded step kernels evaluate it: warp-level BF16 tensor-core
+ * inference (mma.sync m16n8k16, FP32 accumulation; inputs and hidden activations rounded
+ * to BF16) of the network loaded by tc_load_mlp, on B rows of raw features X[B][13]
+ * (device, float32, in the order of tc_mlp.h), writing out[B][3] (device, float32) on
+ * `stream`.  The paper has no counterpart; this is the library's check of its
+ * inference.  Returns TC_EINVAL for B < 0 or NULL arrays, TC_ENOMLP without weights,
+ * TC_ECUDA if the launch fails. */
+int tc_seed_predict(tc_handle *h, const float *X, int B, float *out, void *stream);
+
 /* Counts cells whose status has any TC_ST_ERROR_MASK bit in the last step's status array
  * on `stream` and synchronises it; *nbad receives the count. */
 int tc_sync_status(tc_handle *h, const int *status, long long ncell, void *stream, long long *nbad);

@@ -65,6 +65,17 @@ def forward(theta, x):
     return o, (z1, z2, z3), (x, h1, h2, h3)
 
 
+def forward_bf16_inputs(theta, x):
+    """Outputs o[B, 3] with every layer's inputs rounded to BF16 first (the normalised
+    features and each hidden activation), the rounding of an inference on BF16 tensor
+    cores; sums in FP64."""
+    W1, b1, W2, b2, W3, b3, W4, b4 = unflatten(theta)
+    h = bf16_round(np.asarray(x, dtype=np.float64))
+    for W, b in ((W1, b1), (W2, b2), (W3, b3)):
+        h = bf16_round(silu(h @ W.T + b))
+    return h @ W4.T + b4
+
+
 def loss(theta, x, y, w=(1.0, 1.0, 1.0)):
     o, _, _ = forward(theta, x)
     d = o - np.asarray(y, dtype=np.float64)

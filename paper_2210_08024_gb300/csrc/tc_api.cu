@@ -15,6 +15,7 @@
 #include "../../include/tc_onezone.h"
 #include "../../include/tc_pdr.h"
 #include "tc_launch.h"
+#include "tc_mlp_mma.cuh"
 #include "tc_onezone.cuh"
 #include "tc_order.cuh"
 #include "tc_pdr.cuh"
@@ -61,8 +62,9 @@ struct tc_handle {
   tc_params gp;
   cudaStream_t gstream = nullptr;
   cudaEvent_t gdone = nullptr;
-  // MLP seed weights (device) -- loaded by tc_load_mlp
+  // MLP seed weights (device) -- loaded by tc_load_mlp -- and their tensor-core layout
   void* d_mlp = nullptr;
+  tcg::MlpMma* d_mlp_mma = nullptr;
   size_t mlp_bytes = 0;
   // cost-ordered work queue (tc_params.order_cells): class keys, histogram, order
   unsigned char* d_okey = nullptr;
@@ -80,6 +82,26 @@ struct tc_handle {
   double* d_eqpar = nullptr;
   size_t eqpar_len = 0;
 };
+
+// The step kernel's warp-level tensor-core inference of the seed network on rows of
+// raw features (tc_seed_predict): each warp takes 32 rows at a time, all its lanes
+// together; rows past B are zero features whose outputs are dropped.
+namespace {
+__global__ void __launch_bounds__(128) k_seed_predict(const tcg::MlpMma* __restrict__ m, const float* __restrict__ X,
+                                                      int B, float* __restrict__ out) {
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (long long base = warp * 32; base < B; base += nw * 32) {
+    const long long r = base + lane;
+    float f[tcg::MLP_IN], o[tcg::MLP_OUT];
+    for (int k = 0; k < tcg::MLP_IN; ++k) f[k] = (r < B) ? X[r * tcg::MLP_IN + k] : 0.f;
+    tcg::mlp_infer_warp(m, f, o);
+    if (r < B)
+      for (int j = 0; j < tcg::MLP_OUT; ++j) out[r * tcg::MLP_OUT + j] = o[j];
+  }
+}
+}  // namespace
 
 extern "C" {
 
@@ -155,6 +177,7 @@ void tc_destroy(tc_handle* h) {
   cudaFree(h->d_buf);
   cudaFree(h->d_ibuf);
   cudaFree(h->d_mlp);
+  cudaFree(h->d_mlp_mma);
   cudaFree(h->d_eq);
   cudaFree(h->d_eqi);
   cudaFree(h->d_eqpar);
@@ -304,6 +327,7 @@ static int enqueue(tc_handle* h, bool batch, const tcg::DevFields& f, long long 
   const int grid = sh.grid, block = sh.block;
   if (cudaMemsetAsync(h->d_cursor, 0, sizeof(unsigned long long), st) != cudaSuccess) return TC_ECUDA;
   tcg::DevParams dp = dev_params(h->p);
+  dp.mlp_mma = h->d_mlp_mma;
   // cost-ordered queue: only worth it when the launch holds more cells than a few warps
   if (h->p.order_cells && ntotal > 256 && order_workspace(h, ntotal, st)) {
     if (tcg::launch_order(batch, f, h->d_boxes, dp, dt, ntotal, h->d_okey, h->d_ohist, h->d_order, h->num_sms, st) !=
@@ -555,6 +579,18 @@ int tc_step_batch(tc_handle* h, const tc_fields* boxes, int nbox, double dt_s, v
   return TC_OK;
 }
 
+int tc_seed_predict(tc_handle* h, const float* X, int B, float* out, void* stream) {
+  if (!h || B < 0 || (B > 0 && (!X || !out))) return TC_EINVAL;
+  if (!h->d_mlp_mma) return TC_ENOMLP;
+  if (B == 0) return TC_OK;
+  long long nb = ((long long)B + 127) / 128;
+  if (nb > (long long)h->num_sms * 8) nb = (long long)h->num_sms * 8;
+  k_seed_predict<<<(int)nb, 128, 0, (cudaStream_t)stream>>>(h->d_mlp_mma, X, B, out);
+  if (cudaGetLastError() != cudaSuccess) return TC_ECUDA;
+  h->launches += 1;
+  return TC_OK;
+}
+
 int tc_load_mlp(tc_handle* h, const void* blob, size_t bytes) {
   if (!h || !blob || bytes != sizeof(tcg::MlpDev)) return TC_EINVAL;
   const tcg::MlpDev* hb = (const tcg::MlpDev*)blob;
@@ -562,9 +598,16 @@ int tc_load_mlp(tc_handle* h, const void* blob, size_t bytes) {
       hb->n_in != (uint32_t)tcg::MLP_IN || hb->n_hid != (uint32_t)tcg::MLP_HID || hb->n_out != (uint32_t)tcg::MLP_OUT)
     return TC_EINVAL;
   cudaFree(h->d_mlp);
+  cudaFree(h->d_mlp_mma);
   h->d_mlp = nullptr;
+  h->d_mlp_mma = nullptr;
+  h->mlp_bytes = 0;
   if (cudaMalloc(&h->d_mlp, bytes) != cudaSuccess) return TC_ENOMEM;
+  if (cudaMalloc(&h->d_mlp_mma, sizeof(tcg::MlpMma)) != cudaSuccess) return TC_ENOMEM;
   if (cudaMemcpy(h->d_mlp, blob, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return TC_ECUDA;
+  if (tcg::mlp_mma_layout((const tcg::MlpDev*)h->d_mlp, h->d_mlp_mma, 0) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess)
+    return TC_ECUDA;
   h->mlp_bytes = bytes;
   return TC_OK;
 }

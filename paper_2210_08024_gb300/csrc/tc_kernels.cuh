@@ -19,6 +19,7 @@
 #include <type_traits>
 
 #include "tc_mlp.cuh"
+#include "tc_mlp_mma.cuh"
 #include "tc_phys.cuh"
 
 namespace tcg {
@@ -881,34 +882,40 @@ TCG_FN void substep_mixed(const CellC<double>& c, const CellC<float>& cf, const 
 }
 
 // ------------------------------------------------------------------ seeding (modes 3, 4)
-// Activations of the in-kernel seed inference are stored in FP16 (the seed needs ~1e-2
-// accuracy): 256 bytes of per-thread local memory instead of 512.
-using seed_act_t = __half;
+// Features of a substep's seed: the substep start's state, the per-cell features
+// lf[6] = log10 n, log10 chi_FUV, log10 f_shld,H2, log10(F_LyC+1), log10 xi, log10 Z'_d,
+// the substep length, and the explicit-Euler changes over the substep from the
+// start-state source terms src = (H, C_H2, C_H+) that set its length:
+// g = dts (C_H2 / 0.5, C_H+, H / (K T_mu ln 10)).  Lanes without a substep (need false)
+// get zeros: they take part in the warp's inference and ignore its output.
+TCG_FN void seed_features(const float* lf, const CellC<double>& c, const LaneState& s, double dts, const double* src,
+                          bool need, double* g, float* f) {
+  if (!need) {
+    for (int k = 0; k < MLP_IN; ++k) f[k] = 0.f;
+    g[0] = g[1] = g[2] = 0.0;
+    return;
+  }
+  g[0] = dts * src[1] / 0.5;
+  g[1] = dts * src[2];
+  g[2] = dts * src[0] / (c.K * s.Tmu) / LN10;
+  const float v[MLP_IN] = {lf[0], (float)log10(s.mu * s.Tmu), (float)s.xH2, (float)s.xHp, lf[1], lf[2], lf[3], lf[4],
+                           (float)log10(dts), lf[5], (float)g[0], (float)g[1], (float)g[2]};
+  for (int k = 0; k < MLP_IN; ++k) f[k] = v[k];
+}
 
-// Seed of a substep's Newton iteration from the network.  Features: the substep start's
-// state, the per-cell features lf[6] = log10 n, log10 chi_FUV, log10 f_shld,H2,
-// log10(F_LyC+1), log10 xi, log10 Z'_d, the substep length, and the explicit-Euler
-// changes over the substep from the start-state source terms src = (H, C_H2, C_H+)
-// that set its length: g = dts (C_H2 / 0.5, C_H+, H / (K T_mu ln 10)).  The outputs are
-// the backward-Euler changes of x_H2 (/0.5), x_H+ and log10 T minus those explicit
-// ones, so the prediction is g + output; it is mapped to (T_mu, x_H2, x_H+) with mu
-// frozen at the substep start and clamped inside the admissible region.  Returns false
-// (no seed) if the prediction is not finite or leaves the trust region below.
-TCG_FN bool mlp_seed(const MlpDev* __restrict__ w, seed_act_t* buf0, seed_act_t* buf1, int st, const float* lf,
-                     const CellC<double>& c, const LaneState& s, double dts, const double* src, const DevParams& p,
-                     double* seed) {
-  const double T0 = s.mu * s.Tmu;
-  const double g0 = dts * src[1] / 0.5, g1 = dts * src[2], g2 = dts * src[0] / (c.K * s.Tmu) / LN10;
-  float f[MLP_IN] = {lf[0], (float)log10(T0), (float)s.xH2, (float)s.xHp, lf[1], lf[2], lf[3], lf[4],
-                     (float)log10(dts), lf[5], (float)g0, (float)g1, (float)g2};
-  float o[MLP_OUT];
-  mlp_infer(w, buf0, buf1, st, f, o);
-  const double d0 = g0 + (double)o[0], d1 = g1 + (double)o[1], d2 = g2 + (double)o[2];
+// Seed from the network's outputs o (the backward-Euler changes beyond the explicit
+// ones g): the prediction g + o mapped to (T_mu, x_H2, x_H+) with mu frozen at the
+// substep start and clamped inside the admissible region.  Returns false (no seed) if
+// it is not finite or leaves the trust region below.
+TCG_FN bool seed_from_outputs(const float* o, const double* g, const LaneState& s, const DevParams& p,
+                              double* seed) {
+  const double d0 = g[0] + (double)o[0], d1 = g[1] + (double)o[1], d2 = g[2] + (double)o[2];
   if (!(isfinite(d0) && isfinite(d1) && isfinite(d2))) return false;
   // Trust region: the backward-Euler system can have several roots (thermally unstable
   // gas), and the solver's root is the one Newton reaches from the start state.  A seed
   // is used only when it predicts a small change, inside the basin of that root.
   if (fabs(d2) > SEED_MAX_DLOGT || fabs(0.5 * d0) > SEED_MAX_DX || fabs(d1) > SEED_MAX_DX) return false;
+  const double T0 = s.mu * s.Tmu;
   const double x2 = fmin(fmax(s.xH2 + 0.5 * d0, 1e-20), 0.4999999);
   const double xp = fmin(fmax(s.xHp + d1, 1e-20), 0.999999 * (1.0 - 2.0 * x2));
   const double T1 = fmin(fmax(T0 * exp10(fmin(fmax(d2, -6.0), 6.0)), p.T_floor), 1e10);
@@ -939,20 +946,7 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
   static_assert(LPC == 1 || ((MODE == 1 || MODE == 2) && !BATCH), "cooperative kernels: modes 1 and 2, one box");
   constexpr bool SEEDED = (MODE == 3 || MODE == 4);
   constexpr bool MIXED = (MODE == 2 || MODE == 3);
-  const MlpDev* wsm = nullptr;
-  seed_act_t* buf0 = nullptr;
-  seed_act_t* buf1 = nullptr;
-  // Seed network: the lanes of a warp read the same weight at the same time, so the
-  // weights are read from global memory through L1 (a broadcast) rather than copied to
-  // shared memory; the activations are per-thread arrays.  With no shared memory the
-  // seeded kernels hold as many blocks per SM as the others (136 vs 183 ms for seeded
-  // mixed on the 128^3 slab, against weights and activations in shared memory).
-  seed_act_t act_local[SEEDED ? 2 * MLP_HID : 1];
-  if constexpr (SEEDED) {
-    wsm = mlp;
-    buf0 = act_local;
-    buf1 = act_local + MLP_HID;
-  }
+  (void)mlp;  // the seeded modes read the network in its tensor-core layout, p.mlp_mma
   float lf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   LaneState s;
   CellC<double> c;
@@ -963,84 +957,112 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
   DevFields fb;
   long long li = -1;   // local cell index within its box
   bool have = false;
+  bool done = false;   // the work queue is empty for this lane
   while (true) {
-    if (!have) {
+    if (!have && !done) {
       long long gi = claim_cells_lpc<LPC>(cursor);
-      if (gi >= ntotal) break;
-      if (p.order) gi = (long long)p.order[gi];
-      if (BATCH) {
-        int lo = 0, hi = boxes->nbox - 1;
-        while (lo < hi) {  // last box with start <= gi
-          int mid = (lo + hi + 1) >> 1;
-          if (boxes->start[mid] <= gi) lo = mid; else hi = mid - 1;
+      if (gi >= ntotal) {
+        done = true;
+      } else {
+        if (p.order) gi = (long long)p.order[gi];
+        if (BATCH) {
+          int lo = 0, hi = boxes->nbox - 1;
+          while (lo < hi) {  // last box with start <= gi
+            int mid = (lo + hi + 1) >> 1;
+            if (boxes->start[mid] <= gi) lo = mid; else hi = mid - 1;
+          }
+          fb = boxes->box[lo];
+          li = gi - boxes->start[lo];
+        } else {
+          fb = f1;
+          li = gi;
         }
-        fb = boxes->box[lo];
-        li = gi - boxes->start[lo];
-      } else {
-        fb = f1;
-        li = gi;
+        double T0, x20, xp0;
+        load_cell(fb, li, p, c, T0, x20, xp0);
+        s.t = 0.0;
+        s.xH2 = x20; s.xHp = xp0;
+        s.Td = -1.0;
+        s.nsub = 0;
+        s.status = 0;
+        s.iters = 0;
+        {
+          // initial C/O/e equilibrium (it sets mu and hence T_mu) in FP64 for every mode
+          ChemT<double> b0 = chem_T(c, T0, p.flags);
+          Equil<double> q0 = equilibrium(c, b0, x20, xp0, -1.0);
+          s.xe = q0.xe; s.xCp = q0.xCp; s.xCO = q0.xCO;
+          xe_g = q0.xe;
+          td_g = -1.0;
+        }
+        if constexpr (MIXED) {
+          cf = cast_cell<float>(c);
+          xe_gf = float(s.xe);
+          td_gf = -1.f;
+          td64 = -1.0;
+        }
+        if constexpr (SEEDED) {
+          const double chi_fuv = (1.8e-4 * fb.chi_pe[li] + 3.0e-5 * fb.chi_lw[li]) / 2.1e-4;
+          const double Fl = fb.Flyc ? fb.Flyc[li] : 0.0;
+          lf[0] = (float)log10(fb.n[li]);
+          lf[1] = (float)log10(fmax(chi_fuv, 1e-30));
+          lf[2] = (float)log10(fmax(fb.fh2[li], 1e-30));
+          lf[3] = (float)log10(Fl + 1.0);
+          lf[4] = (float)log10(fmax(fb.xi[li], 1e-30));
+          lf[5] = (float)log10(fmax(fb.Zd ? fb.Zd[li] : fb.Zd_val, 1e-30));
+        }
+        s.mu = c.muH / (1.1 + s.xe - x20);
+        s.Tmu = T0 / s.mu;
+        have = true;
       }
-      double T0, x20, xp0;
-      load_cell(fb, li, p, c, T0, x20, xp0);
-      s.t = 0.0;
-      s.xH2 = x20; s.xHp = xp0;
-      s.Td = -1.0;
-      s.nsub = 0;
-      s.status = 0;
-      s.iters = 0;
-      {
-        // initial C/O/e equilibrium (it sets mu and hence T_mu) in FP64 for every mode
-        ChemT<double> b0 = chem_T(c, T0, p.flags);
-        Equil<double> q0 = equilibrium(c, b0, x20, xp0, -1.0);
-        s.xe = q0.xe; s.xCp = q0.xCp; s.xCO = q0.xCO;
-        xe_g = q0.xe;
-        td_g = -1.0;
-      }
-      if constexpr (MIXED) {
-        cf = cast_cell<float>(c);
-        xe_gf = float(s.xe);
-        td_gf = -1.f;
-        td64 = -1.0;
-      }
-      if constexpr (SEEDED) {
-        const double chi_fuv = (1.8e-4 * fb.chi_pe[li] + 3.0e-5 * fb.chi_lw[li]) / 2.1e-4;
-        const double Fl = fb.Flyc ? fb.Flyc[li] : 0.0;
-        lf[0] = (float)log10(fb.n[li]);
-        lf[1] = (float)log10(fmax(chi_fuv, 1e-30));
-        lf[2] = (float)log10(fmax(fb.fh2[li], 1e-30));
-        lf[3] = (float)log10(Fl + 1.0);
-        lf[4] = (float)log10(fmax(fb.xi[li], 1e-30));
-        lf[5] = (float)log10(fmax(fb.Zd ? fb.Zd[li] : fb.Zd_val, 1e-30));
-      }
-      s.mu = c.muH / (1.1 + s.xe - x20);
-      s.Tmu = T0 / s.mu;
-      have = true;
     }
-    if (s.t < dt) {
-      if (s.nsub >= p.max_sub) {
-        s.status |= ST_MAX_SUB;
-        s.t = dt;
-      } else if constexpr (MODE == 0) {
-        substep_paper(c, p, dt, s);
-      } else if constexpr (MODE == 1) {
-        substep_newton64<LPC>(c, p, dt, s, xe_g, td_g);
-      } else if constexpr (MODE == 2) {
-        substep_mixed<LPC>(c, cf, p, dt, s, xe_gf, td_gf, td64);
-      } else {
-        bool last;
-        double src[3];
-        const double dts = substep_start64(c, p, dt, s, (MODE == 3) ? td64 : td_g, last, src);
+    if constexpr (SEEDED) {
+      // The seed network runs on the warp's tensor cores, an instruction all 32 lanes
+      // issue together: lanes stay in the loop until the whole warp is done.
+      if (__all_sync(0xffffffffu, done)) break;
+      bool need = false, last = false;
+      double dts = 0.0, src[3] = {0.0, 0.0, 0.0}, g[3];
+      if (have && s.t < dt) {
+        if (s.nsub >= p.max_sub) {
+          s.status |= ST_MAX_SUB;
+          s.t = dt;
+        } else {
+          dts = substep_start64(c, p, dt, s, (MODE == 3) ? td64 : td_g, last, src);
+          need = true;
+        }
+      }
+      float feat[MLP_IN], o[MLP_OUT];
+      seed_features(lf, c, s, dts, src, need, g, feat);
+      __syncwarp();
+      mlp_infer_warp(p.mlp_mma, feat, o);
+      if (need) {
         double seed[3];
-        const bool ok = mlp_seed(wsm, buf0, buf1, 1, lf, c, s, dts, src, p, seed);
+        const bool ok = seed_from_outputs(o, g, s, p, seed);
         if constexpr (MODE == 3) substep_mixed_solve(c, cf, p, dt, dts, last, s, xe_gf, td_gf, td64, ok ? seed : nullptr);
         else solve_substep64(c, p, dt, dts, last, s, xe_g, td_g, ok ? seed : nullptr);
+        if (!finite3(s.Tmu, s.xH2, s.xHp)) {
+          s.status |= ST_NONFIN;
+          s.t = dt;
+        }
       }
-      if (!finite3(s.Tmu, s.xH2, s.xHp)) {
-        s.status |= ST_NONFIN;
-        s.t = dt;
+    } else {
+      if (done) break;
+      if (s.t < dt) {
+        if (s.nsub >= p.max_sub) {
+          s.status |= ST_MAX_SUB;
+          s.t = dt;
+        } else if constexpr (MODE == 0) {
+          substep_paper(c, p, dt, s);
+        } else if constexpr (MODE == 1) {
+          substep_newton64<LPC>(c, p, dt, s, xe_g, td_g);
+        } else if constexpr (MODE == 2) {
+          substep_mixed<LPC>(c, cf, p, dt, s, xe_gf, td_gf, td64);
+        }
+        if (!finite3(s.Tmu, s.xH2, s.xHp)) {
+          s.status |= ST_NONFIN;
+          s.t = dt;
+        }
       }
     }
-    if (!(s.t < dt)) {
+    if (have && !(s.t < dt)) {
       store_cell(fb, li, s);
       have = false;
     }

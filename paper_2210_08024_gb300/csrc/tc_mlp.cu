@@ -22,6 +22,44 @@
 #include "../../include/tc.h"
 #include "../../include/tc_mlp.h"
 #include "tc_mlp.cuh"
+#include "tc_mlp_mma.cuh"
+
+namespace tcg {
+namespace {
+// One block of 256 threads: the [out][in] copy of the blob's transposed weights that
+// the tensor-core inference reads as B fragments (tc_mlp_mma.cuh).
+__global__ void k_mlp_mma_layout(const MlpDev* __restrict__ w, MlpMma* __restrict__ m) {
+  for (int i = threadIdx.x; i < MLP_INP; i += blockDim.x) {
+    m->mean[i] = w->in_mean[i];
+    m->inv_std[i] = w->in_inv_std[i];
+  }
+  for (int i = threadIdx.x; i < MLP_HID; i += blockDim.x) {
+    m->b1[i] = w->b1[i];
+    m->b2[i] = w->b2[i];
+    m->b3[i] = w->b3[i];
+  }
+  for (int i = threadIdx.x; i < 8; i += blockDim.x) m->b4[i] = (i < MLP_OUT) ? w->b4[i] : 0.f;
+  for (int i = threadIdx.x; i < MLP_HID * MLP_INP; i += blockDim.x) {
+    const int o = i / MLP_INP, k = i % MLP_INP;
+    m->W1[i] = w->W1t[k * MLP_HID + o];
+  }
+  for (int i = threadIdx.x; i < MLP_HID * MLP_HID; i += blockDim.x) {
+    const int o = i / MLP_HID, k = i % MLP_HID;
+    m->W2[i] = w->W2t[k * MLP_HID + o];
+    m->W3[i] = w->W3t[k * MLP_HID + o];
+  }
+  for (int i = threadIdx.x; i < 8 * MLP_HID; i += blockDim.x) {
+    const int o = i / MLP_HID, k = i % MLP_HID;
+    m->W4[i] = (o < MLP_OUT) ? w->W4t[k * 4 + o] : __float2bfloat16_rn(0.f);
+  }
+}
+}  // namespace
+
+cudaError_t mlp_mma_layout(const MlpDev* w, MlpMma* m, cudaStream_t st) {
+  k_mlp_mma_layout<<<1, 256, 0, st>>>(w, m);
+  return cudaGetLastError();
+}
+}  // namespace tcg
 
 namespace {
 

@@ -70,12 +70,15 @@ TCG_FN float m_abs(float a) { return fabsf(a); }
 template <class F> TCG_FN F logistic(F z) { return F(1) / (F(1) + m_exp(-z)); }
 
 // Parameters copied to the device by value with each launch.
+struct MlpMma;  // seed network in the tensor-core layout (tc_mlp_mma.cuh)
+
 struct DevParams {
   double dvdr_kms_pc, T_cmb, chi0, opt_over_fuv, tau_ratio;
   double limiter, fd_rel, rtol, rtol_mixed, T_floor;
   int newton_max, max_sub;
   unsigned flags;
   const unsigned* order = nullptr;  // optional: the k-th claimed cell is order[k] (cost-ordered queue)
+  const MlpMma* mlp_mma = nullptr;  // seeded modes: the network for the warp-level inference
 };
 
 // ------------------------------------------------------------------ per-cell constants

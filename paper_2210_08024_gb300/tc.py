@@ -121,6 +121,7 @@ def _load():
     L.tc_create.argtypes = [ctypes.POINTER(tc_params), ctypes.POINTER(ctypes.c_void_p)]
     L.tc_step.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_double, ctypes.c_void_p]
     L.tc_step_host.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_double, ctypes.c_void_p]
+    L.tc_seed_predict.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     L.tc_rates.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_double, ctypes.c_void_p,
                            ctypes.c_void_p, ctypes.c_void_p]
     L.tc_autotune.argtypes = [ctypes.c_void_p, ctypes.POINTER(tc_fields), ctypes.c_double, ctypes.c_void_p,
@@ -252,6 +253,12 @@ def make_host_fields(arrs: dict, Zg: float = 1.0, Zd: float = 1.0) -> tc_fields:
     f.Zg_val = float(Zg)
     f.Zd_val = float(Zd)
     return f
+
+
+def tc_seed_predict(h, X, out, stream=None) -> None:
+    """The seeded kernels' tensor-core inference of the loaded network on X (device
+    float32 [B, 13]) into out (device float32 [B, 3])."""
+    _check(lib.tc_seed_predict(h, _ptr(X), int(X.shape[0]), _ptr(out), _stream_ptr(stream)), "tc_seed_predict")
 
 
 def tc_rates(h, fields: tc_fields, dt: float, rate=None, dts=None, stream=None) -> None:
