@@ -589,13 +589,122 @@ constexpr int SEED_MAXIT = 6;
 // Largest predicted changes (log10 T, abundances) for which a seed is used.
 constexpr float SEED_MAX_DLOGT = 0.02f, SEED_MAX_DX = 0.02f;
 
+// f(y) from FP32 source terms; the closure x_H and the net sums H = n G - n^2 L,
+// C_H2 = form - dest, C_H+ = ion - rec are formed in FP64 from the FP32 parts.
+TCG_FN void feval32(const CellC<float>& cf, const ChemT<float>& b, const CoolT<float>& k, double y1, double y2,
+                    double Kinv, float& xe_guess, float& td_guess, double* f) {
+  const double xH = 1.0 - 2.0 * y1 - y2;
+  Equil<float> q = equilibrium(cf, b, float(y1), float(y2), xe_guess);
+  Src<float> s = source(cf, b, k, float(y1), float(y2), float(xH), q, -1.f, td_guess);
+  xe_guess = q.xe;
+  td_guess = s.Td;
+  const double n = double(cf.n);
+  f[0] = (n * double(s.G) - n * n * double(s.L)) * Kinv;
+  f[1] = double(s.form) - double(s.dest);
+  f[2] = double(s.ion) - double(s.rec);
+}
+
+// FP32 forward-difference Jacobian (relative step 1e-3) of the backward-Euler residual
+// at y, built afresh at the FP32 iteration's root before the FP64 polish: at the root
+// itself it is as good as an FP32 difference gets (~1e-3), so the polish contracts by
+// about that much per correction instead of by the error of a Jacobian built several
+// iterations earlier.  With LPC = 4 the four evaluations are split over the cell's lanes.
+template <int LPC = 1>
+TCG_FN void fd_jacobian32(const CellC<float>& cf, const DevParams& p, double mu, double Kinv, double dts,
+                          const double* y, float xe_g, float td_g, double J[3][3]) {
+  const double h0 = 1e-3 * y[0];
+  const double h1 = fmax(1e-3 * fabs(y[1]), 1e-12), h2 = fmax(1e-3 * fabs(y[2]), 1e-12);
+  double f0[3], f1[3], f2[3], fT[3];
+  if constexpr (LPC == 4) {
+    const int q = lane_in_cell<LPC>();
+    double fq[3];
+    float xg = xe_g, tg = td_g;
+    {
+      ChemT<float> b = chem_T(cf, float(mu * ((q == 3) ? y[0] + h0 : y[0])), p.flags);
+      CoolT<float> k = cool_T(cf, b, p.flags);
+      feval32(cf, b, k, y[1] + ((q == 1) ? h1 : 0.0), y[2] + ((q == 2) ? h2 : 0.0), Kinv, xg, tg, fq);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      f0[i] = from_lane<LPC>(fq[i], 0);
+      f1[i] = from_lane<LPC>(fq[i], 1);
+      f2[i] = from_lane<LPC>(fq[i], 2);
+      fT[i] = from_lane<LPC>(fq[i], 3);
+    }
+  } else {
+    ChemT<float> b = chem_T(cf, float(mu * y[0]), p.flags);
+    CoolT<float> k = cool_T(cf, b, p.flags);
+    float xg = xe_g, tg = td_g;
+    feval32(cf, b, k, y[1], y[2], Kinv, xg, tg, f0);
+    xg = xe_g; tg = td_g;
+    feval32(cf, b, k, y[1] + h1, y[2], Kinv, xg, tg, f1);
+    xg = xe_g; tg = td_g;
+    feval32(cf, b, k, y[1], y[2] + h2, Kinv, xg, tg, f2);
+    ChemT<float> bT = chem_T(cf, float(mu * (y[0] + h0)), p.flags);
+    CoolT<float> kT = cool_T(cf, bT, p.flags);
+    xg = xe_g; tg = td_g;
+    feval32(cf, bT, kT, y[1], y[2], Kinv, xg, tg, fT);
+  }
+  const double s0 = dts / h0, s1 = dts / h1, s2 = dts / h2;
+  for (int i = 0; i < 3; ++i) {
+    J[i][0] = ((i == 0) ? 1.0 : 0.0) - s0 * (fT[i] - f0[i]);
+    J[i][1] = ((i == 1) ? 1.0 : 0.0) - s1 * (f1[i] - f0[i]);
+    J[i][2] = ((i == 2) ? 1.0 : 0.0) - s2 * (f2[i] - f0[i]);
+  }
+}
+
+// Seeded FP64 solve (mode 4): FP64 chord iterations from the seed with the FP32
+// forward-difference Jacobian built at the seed.  The network puts the seed within
+// ~2e-4 of the root, so each iteration contracts by about the Jacobian's error (~1e-3)
+// and the FP64 residual brings the iterate to the FP64 root in a few evaluations of f,
+// with the convergence test of the FP64 Newton solve (every step below rtol |y_i|).
+// Returns the iterations, or -1 if a step fails to contract by half, the state is not
+// finite, or SEED_MAXIT + 2 iterations pass; `spent` receives the iterations made.
+template <int LPC = 1>
+TCG_FN int chord64_from_seed(const CellC<double>& c, const CellC<float>& cf, const DevParams& p, double mu, double Kinv,
+                             const double* yn, double dts, double* y, double& xe_g, double& td_g, Equil<double>* qb,
+                             int* spent) {
+  double J[3][3];
+  fd_jacobian32<LPC>(cf, p, mu, Kinv, dts, y, float(xe_g), float(td_g), J);
+  double prev = -1.0;
+  for (int it = 1; it <= SEED_MAXIT + 2; ++it) {
+    TCG_COUNT_D(chord64_it);
+    *spent = it;
+    ChemT<double> b = chem_T(c, mu * y[0], p.flags);
+    CoolT<double> k = cool_T(c, b, p.flags);
+    double f0[3];
+    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, qb);
+    double Jw[3][3], rhs[3], d[3];
+    for (int i = 0; i < 3; ++i) {
+      rhs[i] = -(y[i] - yn[i] - dts * f0[i]);
+      for (int jj = 0; jj < 3; ++jj) Jw[i][jj] = J[i][jj];
+    }
+    if (!solve3<double>(Jw, rhs, d)) return -1;
+    double st[3];
+    const bool full = damped_step(y, d, st);
+    if (!finite3(y[0], y[1], y[2])) return -1;
+    bool conv = full;
+    double nrm = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      if (fabs(st[i]) > p.rtol * fabs(y[i]) + 1e-300) conv = false;
+      nrm = fmax(nrm, fabs(st[i]) / (fabs(y[i]) + 1e-300));
+    }
+    if (conv) return it;
+    if (prev > 0.0 && nrm > 0.5 * prev) return -1;
+    prev = nrm;
+  }
+  return -1;
+}
+
+
 // Solves one substep of length dts by the FP64 Newton iteration, from `seed` when
 // given (the root is the same; a seeded solve that fails is retried from the start
 // state), else from the start state, then from the predictor; a substep that fails
 // from both is retried at half length (up to 30 times) and the cell flagged ST_NEWTON.
 template <int LPC = 1>
 TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double dt, double dts, bool last,
-                            LaneState& s, double& xe_g, double& td_g, const double* seed = nullptr) {
+                            LaneState& s, double& xe_g, double& td_g, const double* seed = nullptr,
+                            const CellC<float>* cf = nullptr) {
   const double yn[3] = {s.Tmu, s.xH2, s.xHp};
   const double Kinv = 1.0 / c.K;
   double y[3] = {yn[0], yn[1], yn[2]};
@@ -605,7 +714,8 @@ TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double d
     y[0] = seed[0]; y[1] = seed[1]; y[2] = seed[2];
     double xg = xe_g, tg = td_g;
     int spent = 0;
-    it = newton_solve<LPC>(c, p, s.mu, Kinv, yn, dts, y, xg, tg, SEED_MAXIT, &qb, &spent);
+    it = cf ? chord64_from_seed<LPC>(c, *cf, p, s.mu, Kinv, yn, dts, y, xg, tg, &qb, &spent)
+            : newton_solve<LPC>(c, p, s.mu, Kinv, yn, dts, y, xg, tg, SEED_MAXIT, &qb, &spent);
     if (it >= 0) {
       xe_g = xg; td_g = tg;
       s.status |= ST_SEEDED;
@@ -651,21 +761,6 @@ TCG_FN void substep_newton64(const CellC<double>& c, const DevParams& p, double 
 }
 
 // ------------------------------------------------------------------ mode 2: mixed precision
-// f(y) from FP32 source terms; the closure x_H and the net sums H = n G - n^2 L,
-// C_H2 = form - dest, C_H+ = ion - rec are formed in FP64 from the FP32 parts.
-TCG_FN void feval32(const CellC<float>& cf, const ChemT<float>& b, const CoolT<float>& k, double y1, double y2,
-                    double Kinv, float& xe_guess, float& td_guess, double* f) {
-  const double xH = 1.0 - 2.0 * y1 - y2;
-  Equil<float> q = equilibrium(cf, b, float(y1), float(y2), xe_guess);
-  Src<float> s = source(cf, b, k, float(y1), float(y2), float(xH), q, -1.f, td_guess);
-  xe_guess = q.xe;
-  td_guess = s.Td;
-  const double n = double(cf.n);
-  f[0] = (n * double(s.G) - n * n * double(s.L)) * Kinv;
-  f[1] = double(s.form) - double(s.dest);
-  f[2] = double(s.ion) - double(s.rec);
-}
-
 // Mixed Newton on the same residual: FP32 source evaluations, FP64 residual, solve and
 // update.  The forward-difference Jacobian (relative step 1e-3, large enough that FP32
 // rounding in f stays ~1e-4 of each column) is built at the first iteration and reused;
@@ -779,16 +874,17 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
 // the FP64 one by the FP32 rounding floor of f (~1e-6 relative in T near stiff
 // equilibria, where H is a small difference of large terms), and the scheme can
 // amplify such errors a hundredfold over a step, so every substep is polished.
-// A chord iteration contracts by the Jacobian's relative error rho (~1e-3 for the FP32
-// forward differences of relative step 1e-3, worse near stiff equilibria), so after a
-// correction d_k the remaining error is about rho d_k / (1 - rho), with rho estimated as
-// d_k / d_(k-1).  Accepted when that estimate is below 1e-9 relative (abundances
-// relative to max(x, 1e-4)), or when a correction is itself below 1e-8 (on the slab the
-// first correction has a median of 3e-8 and rho a median of 0.015, 0.11 at the 90th
-// percentile); after at most five corrections, otherwise the FP64 solver takes the
-// substep.  Measured on 4 x 4096 random-state cells, largest error in T against the
-// FP64 oracle after one step, by the threshold for a single correction: 1e-7: 1.05e-5
-// (1.13 corrections per slab substep); 3e-8: 7.3e-6 (1.46); 1e-8: 4.6e-6 (1.83).
+// The Jacobian is the FP32 forward difference built at the FP32 root (fd_jacobian32).
+// A chord iteration contracts by the Jacobian's relative error rho (~1e-3 there), so
+// after a correction d_k the remaining error is about rho d_k / (1 - rho), with rho
+// estimated as d_k / d_(k-1).  Accepted when that estimate is below 1e-9 relative
+// (abundances relative to max(x, 1e-4)), or when a single correction is below 1e-7;
+// after at most five corrections, otherwise the FP64 solver takes the substep.
+// Measured on 4 x 4096 random-state cells, largest error in T against the FP64 oracle
+// after one step, and FP64 polish evaluations per slab substep:
+//   Jacobian from the FP32 iteration, single correction below 1e-8: 4.6e-6, 1.83
+//   (below 1e-7: 1.05e-5, 1.13, over the bound);
+//   Jacobian rebuilt at the FP32 root, single correction below 1e-7: 1.1e-6, 1.14.
 // `qlast` receives the C/O/e equilibrium of the last FP64 evaluation.
 TCG_FN bool polish64(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
                      double dts, double* y, const double J[3][3], double& xe_g, double& td_g, Equil<double>& qlast) {
@@ -817,7 +913,7 @@ TCG_FN bool polish64(const CellC<double>& c, const DevParams& p, double mu, doub
       prev = -1.0;
       continue;
     }
-    if (nrm <= 1e-8) return true;
+    if (nrm <= 1e-7) return true;
     if (prev > 0.0) {
       const double rho = nrm / prev;
       if (rho < 0.5 && rho * nrm <= 1e-9 * (1.0 - rho)) return true;
@@ -858,6 +954,7 @@ TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<float>& cf, 
   Equil<double> qlast;
   if (it >= 0) {
     if (polish) s.status |= ST_POLISH;
+    fd_jacobian32<LPC>(cf, p, s.mu, Kinv, dts, y, xe_g, td_g, J);
     double xg = double(xe_g), tg = double(td_g);
     if (!polish64(c, p, s.mu, Kinv, yn, dts, y, J, xg, tg, qlast)) it = -1;
   }
@@ -993,7 +1090,7 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
           xe_g = q0.xe;
           td_g = -1.0;
         }
-        if constexpr (MIXED) {
+        if constexpr (MIXED || SEEDED) {
           cf = cast_cell<float>(c);
           xe_gf = float(s.xe);
           td_gf = -1.f;
@@ -1037,7 +1134,7 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
         double seed[3];
         const bool ok = seed_from_outputs(o, g, s, p, seed);
         if constexpr (MODE == 3) substep_mixed_solve(c, cf, p, dt, dts, last, s, xe_gf, td_gf, td64, ok ? seed : nullptr);
-        else solve_substep64(c, p, dt, dts, last, s, xe_g, td_g, ok ? seed : nullptr);
+        else solve_substep64(c, p, dt, dts, last, s, xe_g, td_g, ok ? seed : nullptr, &cf);
         if (!finite3(s.Tmu, s.xH2, s.xHp)) {
           s.status |= ST_NONFIN;
           s.t = dt;
