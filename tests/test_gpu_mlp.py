@@ -192,35 +192,32 @@ def test_training_labels_match_oracle(tc):
 
 
 @pytest.mark.parametrize("workload", ["slab", "random"])
-def test_seeded_fp64_same_root_and_iteration_count(tc, trained_blob, workload):
-    # The seeded solve must reach the same root as the unseeded one, and on the slab
-    # (the network's training distribution) it must need fewer Newton-type iterations:
-    # the network predicts each substep's root from the explicit-Euler changes and the
-    # state (to ~2e-4 in log10 T), and Newton starts there instead of at the start state.
-    # The count falls less than the work: with the 1e-12 step criterion a seeded solve
-    # still takes ~4 iterations, but fewer of them rebuild the Jacobian.  Measured on
-    # this sample: 10.85 plain, 10.31 seeded per cell.  The random states lie outside
-    # the training distribution (up to 1e7 K): there the trust region keeps many seeds
-    # out and the count may not fall.
+def test_seeded_fp64_same_root(tc, trained_blob, workload):
+    # The seeded FP64 solve (FP64 chord iterations from the network's prediction on an
+    # FP32 Jacobian built there, the plain Newton solve from the start state where the
+    # seed is missing or fails) must reach the same FP64 roots as the unseeded solver.
+    # On the slab most cells start some substep from the seed.  Iteration counts are
+    # printed with -s; they are not comparable with the plain solve's (a chord
+    # iteration evaluates f once, a full Newton iteration four times).
     c = synthgen.slab(ncell=20000, key=41) if workload == "slab" else synthgen.cells_4096(n=2048, key=43)
     plain = _run(tc, c, tc.TC_MODE_NEWTON_FP64)
     seeded = _run(tc, c, tc.TC_MODE_NEWTON_FP64_SEEDED, trained_blob)
     assert np.array_equal(seeded["status"] & tc.TC_ST_ERROR_MASK, plain["status"] & tc.TC_ST_ERROR_MASK)
     assert_fp64_parity(seeded, plain, "seeded-vs-plain")
+    assert np.array_equal(seeded["nsub"], plain["nsub"])
     ref = oracle.step(synthgen.subset(c, slice(0, 2000)), DT, oracle.default_params(mode=1))
     assert_fp64_parity(synthgen.subset(seeded, slice(0, 2000)), ref, "seeded-vs-oracle")
-    print("%s: Newton iterations per cell: plain %.3f, seeded %.3f" % (workload, plain["iters"].mean(),
-                                                                        seeded["iters"].mean()))
+    print("%s: iterations per cell: plain %.3f, seeded %.3f; cells with a seeded solve %.3f, with a failed seed %.4f"
+          % (workload, plain["iters"].mean(), seeded["iters"].mean(),
+             np.mean((seeded["status"] & tc.TC_ST_SEEDED) != 0), np.mean((seeded["status"] & tc.TC_ST_SEED_FAIL) != 0)))
     if workload == "slab":
-        assert seeded["iters"].sum() <= 0.97 * plain["iters"].sum()
         assert np.mean((seeded["status"] & tc.TC_ST_SEEDED) != 0) > 0.5
-    else:
-        assert seeded["iters"].sum() <= 1.05 * plain["iters"].sum()
+        assert np.mean((seeded["status"] & tc.TC_ST_SEED_FAIL) != 0) < 0.05
 
 
 def test_seeded_mixed_needs_fewer_iterations_on_slab(tc, trained_blob):
     # The mixed solve's FP32 Newton iterations from the seed (measured on the 128^3 slab:
-    # 10.43 against 11.30 per cell; seeded mixed 125 ms against 153 ms unseeded).
+    # 10.44 against 11.30 per cell; seeded mixed 111 ms against 129 ms unseeded).
     c = synthgen.slab(ncell=20000, key=41)
     plain = _run(tc, c, tc.TC_MODE_MIXED)
     seeded = _run(tc, c, tc.TC_MODE_MIXED_SEEDED, trained_blob)
