@@ -181,7 +181,8 @@ def measure_peaks(tc, torch):
     rates = {}
     for name, kind, it in (("fma", 0, iters), ("exp", 2, iters // 16), ("log", 3, iters // 16),
                            ("sqrt", 4, iters // 8), ("div", 5, iters // 8), ("pow", 6, iters // 32),
-                           ("fma32", 1, iters * 8), ("mufu", 8, iters * 2)):
+                           ("fma32", 1, iters * 8), ("mufu", 8, iters * 2), ("df64_muladd", 9, iters),
+                           ("df64_exp", 10, iters // 16)):
         tc.tc_peak_launch(kind, grid, block, it, sink)
         torch.cuda.synchronize()
         best = None
@@ -199,7 +200,9 @@ def measure_peaks(tc, torch):
     for k in ("div", "sqrt", "exp", "log", "pow"):
         weights[k] = fma / rates[k]
     return {"fp64_fma_per_s": fma, "fp32_fma_per_s": rates["fma32"], "mufu_per_s": rates["mufu"], "rates": rates,
-            "weights": weights}
+            "weights": weights,
+            # df64 (double-float) operations against their FP64 counterparts on this GPU
+            "df64_vs_fp64": {"muladd": rates["df64_muladd"] / fma, "exp": rates["df64_exp"] / rates["exp"]}}
 
 
 def flops_per_cell(counts: dict, weights: dict) -> float:
@@ -592,7 +595,7 @@ def report(args, results, head, ncell, peaks, e2e, clocks, cells, ws):
             rr["fp64_tflops"] = rl["achieved"]
             rr["algorithmic_per_cell"] = algo[MODE_WORK[name]]
             if MODE_WORK[name] == "mode2":
-                rr["fp32_pipes"] = fp32_fractions(work["mode2_fp32"], rr, ncell, peaks)
+                rr["fp32_pipes"] = fp32_fractions(work["mode2_fp32"], work["mode2_df64"], rr, ncell, peaks)
     cpu = None if args.no_cpu_baseline else cpu_baseline(cells, head)
     out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
@@ -609,24 +612,29 @@ def report(args, results, head, ncell, peaks, e2e, clocks, cells, ws):
                "fp64_tflops": 2.0 * peaks["fp64_fma_per_s"] / 1e12,
                "fp32_tflops": 2.0 * peaks["fp32_fma_per_s"] / 1e12,
                "mufu_ops_per_s": peaks["mufu_per_s"],
+               "df64_vs_fp64": peaks["df64_vs_fp64"],
                "fma_slot_weights": peaks["weights"]},
            "cpu_baseline": cpu}
     return out
 
 
-def fp32_fractions(w32, r, ncell, peaks):
-    """FP32 side of a mixed launch: FP32 flops (add and multiply, plus the multiply that
-    accompanies each approximate exp, log, sqrt and divide) against the measured FP32 FMA
-    rate, and MUFU operations (one per exp, log, sqrt and divide of the fast-math build)
-    against the measured MUFU rate.  The counts are the slab's per-cell FP32 work
-    (work_slab128.json, mode2_fp32) times the cells of the launch."""
+def fp32_fractions(w32, w_df, r, ncell, peaks):
+    """FP32 side of a mixed launch.  FP32 work: the FP32 evaluations' flops (add and
+    multiply, plus the multiply that accompanies each approximate exp, log, sqrt and
+    divide) and the df64 evaluations' FP32-pipe instructions (work_slab128.json,
+    mode2_df64.fp32_inst: each df64 operation class times its instruction count),
+    against the measured FP32 FMA issue rate (one instruction per lane and clock).  MUFU
+    operations (one per exp, log, sqrt and divide of the fast-math FP32 evaluations)
+    against the measured MUFU rate.  Counts per slab cell times the cells of the launch."""
     t = r["kernel_ms"] * 1e-3
     special = sum(w32[k] for k in ("div", "sqrt", "exp", "log"))
-    fl = (w32["add"] + w32["mul"] + special) * ncell
+    inst = (w32["add"] + w32["mul"] + special + w_df["fp32_inst"]) * ncell
     mufu = special * ncell
-    return {"fp32_tflops": fl / t / 1e12, "fp32_frac": fl / t / (2.0 * peaks["fp32_fma_per_s"]),
+    return {"fp32_inst_per_s": inst / t, "fp32_frac": inst / t / peaks["fp32_fma_per_s"],
+            "df64_share_of_fp32_inst": w_df["fp32_inst"] / (w32["add"] + w32["mul"] + special + w_df["fp32_inst"]),
             "mufu_ops_per_s": mufu / t, "mufu_frac": mufu / t / peaks["mufu_per_s"],
-            "work": "FP32 ops per cell of the library's mixed step (work_slab128.json, mode2_fp32) x %d cells" % ncell}
+            "work": "FP32 ops and df64 FP32 instructions per cell of the library's mixed step (work_slab128.json, "
+                    "mode2_fp32, mode2_df64) x %d cells" % ncell}
 
 
 def roofline_of(work, r, mode, ncell, peaks):

@@ -16,7 +16,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtc_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["tc_api.cu", "tc_onezone.cu", "tc_sixray.cu", "tc_pdr.cu", "tc_order.cu", "tc_k_paper.cu", "tc_k_newton.cu", "tc_k_mixed.cu", "tc_mlp.cu", "tc_peak.cu",
-           "tc_static.cu", "tc_k_seeded3.cu", "tc_k_seeded4.cu", "tc_k_newton_coop.cu", "tc_k_mixed_coop.cu"]
+           "tc_static.cu", "tc_k_seeded3.cu", "tc_k_seeded4.cu", "tc_k_newton_coop.cu", "tc_k_mixed_coop.cu",
+           "tc_df64_diag.cu"]
 
 
 def nvcc() -> str:
@@ -31,11 +32,14 @@ def _flags():
 
 
 # The mixed-precision step kernels evaluate their Newton iterations on FP32 source terms
-# and correct every root with an FP64 polish, so their FP32 arithmetic may use the fast
-# approximate intrinsics (exp, log, divide; flush-to-zero).  This changes no FP64
-# operation.  Measured on the 128^3 slab: mixed 250 -> 215 ms, mixed + seed 295 ->
-# 238 ms, with the same iteration counts and the same parity results.
-FAST_FP32 = {"tc_k_mixed.cu", "tc_k_seeded3.cu", "tc_k_mixed_coop.cu"}
+# and correct every root with a high-precision polish, so their FP32 arithmetic may use
+# the fast approximate intrinsics (exp, log, divide; flush-to-zero).  This changes no
+# FP64 operation, and the df64 arithmetic of the polish (tc_df64.cuh) uses rounded
+# intrinsics for its error-free transformations and corrects its FP32 first
+# approximations.  Measured on the 128^3 slab (with an FP64 polish): mixed 250 -> 215 ms,
+# mixed + seed 295 -> 238 ms, with the same iteration counts and the same parity results.
+# tc_df64_diag.cu holds the device check of the df64 arithmetic, built the same way.
+FAST_FP32 = {"tc_k_mixed.cu", "tc_k_seeded3.cu", "tc_k_mixed_coop.cu", "tc_df64_diag.cu"}
 
 
 def _compile(src: str) -> tuple[str, str]:

@@ -1,0 +1,289 @@
+// Double-float ("df64") arithmetic on the FP32 pipes, for the high-precision parts of the
+// mixed-precision step (the polish of each root and the source terms that set each
+// substep's length).
+//
+// A value is the unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi)/2:
+// about 44-48 significant bits (relative rounding 4e-15 to 6e-14 per operation; FP64's
+// is 1.1e-16) over FP32's exponent range.  On a GB300 one FP64 operation takes as much
+// of its pipe as ~75 FP32 operations take of theirs (measured FP64 FMA rate ~1 TFLOP/s
+// against ~77 TFLOP/s FP32), so an operation of ~10 FP32 instructions is several times
+// cheaper than its FP64 counterpart; the step's FP64 work is dominated by exp and
+// division, which gain most.
+//
+// Methods (published, restated here):
+//  - error-free transformations: Knuth's TwoSum, Dekker's fast two-sum (|a| >= |b|), and
+//    the exact product error by a fused multiply-add (Dekker's product, FMA form);
+//  - addition and multiplication in the "sloppy" double-double forms of Hida, Li and
+//    Bailey (2001): one error-free transformation on the leading parts, the trailing
+//    parts added in plain arithmetic, one renormalisation;
+//  - division by long division: q1 = a/b in FP32, the remainder a - b q1 in df64, a
+//    second FP32 quotient of the remainder (FP32 quotients good to 2 units in the last
+//    place, as the fast-math build's divide, give ~2^-44);
+//  - square root by one Newton correction of the FP32 root;
+//  - exp by Cody-Waite argument reduction x = k ln2/16 + r (ln2/16 in three FP32 pieces,
+//    the first with 12 significant bits so that k times it is exact for |k| < 2^12),
+//    2^(j/16) from a 16-entry table of df64 values (j = k mod 16), and the Taylor series
+//    of exp(r) - 1 to r^6 for |r| <= ln2/32 (truncation error below 5e-16);
+//  - log by one correction of the FP32 logarithm y0: with d = x exp(-y0) - 1 (small),
+//    log x = y0 + log(1 + d) = y0 + d - d^2/2 + d^3/3 (error ~d^4/4, below 1e-19).
+// Infinities would turn the trailing parts into NaN (inf - inf in the error-free
+// transformations), so the type saturates instead: a conversion from FP64 maps
+// magnitudes above 1e36 (and infinities) to +-1e36, exp returns 0 below -87 (FP32's
+// range, flushed to zero) and exp(80) above 80, and log(0) returns -1e36.  Values that
+// large or small only enter the step's terms where the FP64 result is 0 or saturated
+// too (no CO formation, an infinite velocity-gradient column), and there they change
+// the result by less than 1e-30 relative.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#ifndef TCG_FN
+#define TCG_FN __host__ __device__ __forceinline__
+#endif
+
+namespace tcg {
+
+// ------------------------------------------------------------------ FP32 primitives
+// On the device the rounded intrinsics keep the compiler from contracting or
+// reassociating the error-free transformations (also in fast-math builds); on the host
+// the library is compiled without floating-point contraction.
+TCG_FN float df_add_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+TCG_FN float df_sub_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fsub_rn(a, b);
+#else
+  return a - b;
+#endif
+}
+TCG_FN float df_mul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+TCG_FN float df_fma(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return __fmaf_rn(a, b, c);
+#else
+  return fmaf(a, b, c);
+#endif
+}
+// Correctly rounded FP32 reciprocal (the first quotient digit of a division).
+TCG_FN float df_rcp(float a) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(a);
+#else
+  return 1.0f / a;
+#endif
+}
+// 2^m for -126 <= m <= 127.
+TCG_FN float df_pow2i(int m) {
+#ifdef __CUDA_ARCH__
+  return __int_as_float((m + 127) << 23);
+#else
+  return ldexpf(1.0f, m);
+#endif
+}
+
+// s + e = a + b exactly (Knuth).
+TCG_FN void two_sum(float a, float b, float& s, float& e) {
+  s = df_add_rn(a, b);
+  const float bb = df_sub_rn(s, a);
+  e = df_add_rn(df_sub_rn(a, df_sub_rn(s, bb)), df_sub_rn(b, bb));
+}
+// s + e = a + b exactly when |a| >= |b| (Dekker).
+TCG_FN void fast_two_sum(float a, float b, float& s, float& e) {
+  s = df_add_rn(a, b);
+  e = df_sub_rn(b, df_sub_rn(s, a));
+}
+// p + e = a b exactly (barring underflow).
+TCG_FN void two_prod(float a, float b, float& p, float& e) {
+  p = df_mul_rn(a, b);
+  e = df_fma(a, b, -p);
+}
+
+// ------------------------------------------------------------------ the type
+constexpr double DF_BIG = 1e36;
+
+struct df64 {
+  float hi, lo;
+  df64() = default;
+  // From FP64: the leading 48 bits, split exactly; magnitudes above DF_BIG saturate.
+  TCG_FN constexpr df64(double x)
+      : hi((x > DF_BIG) ? float(DF_BIG) : (x < -DF_BIG) ? float(-DF_BIG) : float(x)),
+        lo((x > DF_BIG || x < -DF_BIG) ? 0.0f : float(x - double(float(x)))) {}
+  TCG_FN static df64 make(float h, float l) {
+    df64 r;
+    r.hi = h;
+    r.lo = l;
+    return r;
+  }
+  TCG_FN explicit operator double() const { return double(hi) + double(lo); }
+};
+
+TCG_FN df64 operator-(df64 a) { return df64::make(-a.hi, -a.lo); }
+
+TCG_FN df64 operator+(df64 a, df64 b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = df_add_rn(e, df_add_rn(a.lo, b.lo));
+  float h, l;
+  fast_two_sum(s, e, h, l);
+  return df64::make(h, l);
+}
+TCG_FN df64 operator-(df64 a, df64 b) { return a + (-b); }
+
+TCG_FN df64 operator*(df64 a, df64 b) {
+  float p, e;
+  two_prod(a.hi, b.hi, p, e);
+  e = df_fma(a.hi, b.lo, e);
+  e = df_fma(a.lo, b.hi, e);
+  float h, l;
+  fast_two_sum(p, e, h, l);
+  return df64::make(h, l);
+}
+// df64 times an FP32 number
+TCG_FN df64 mul_f(df64 a, float b) {
+  float p, e;
+  two_prod(a.hi, b, p, e);
+  e = df_fma(a.lo, b, e);
+  float h, l;
+  fast_two_sum(p, e, h, l);
+  return df64::make(h, l);
+}
+// df64 plus an FP32 number
+TCG_FN df64 add_f(df64 a, float b) {
+  float s, e;
+  two_sum(a.hi, b, s, e);
+  e = df_add_rn(e, a.lo);
+  float h, l;
+  fast_two_sum(s, e, h, l);
+  return df64::make(h, l);
+}
+
+// The quotients are FP32 divisions, not products with a reciprocal: the reciprocal of
+// a subnormal divisor overflows, and 0 times it would give NaN where the quotient is 0.
+TCG_FN df64 operator/(df64 a, df64 b) {
+  const float q1 = a.hi / b.hi;
+  const df64 r = a - mul_f(b, q1);  // the remainder, ~2^-22 of a
+  const float q2 = r.hi / b.hi;
+  float h, l;
+  fast_two_sum(q1, q2, h, l);
+  return df64::make(h, l);
+}
+
+TCG_FN df64& operator+=(df64& a, df64 b) { a = a + b; return a; }
+TCG_FN df64& operator-=(df64& a, df64 b) { a = a - b; return a; }
+TCG_FN df64& operator*=(df64& a, df64 b) { a = a * b; return a; }
+
+TCG_FN bool operator<(df64 a, df64 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+TCG_FN bool operator>(df64 a, df64 b) { return b < a; }
+TCG_FN bool operator<=(df64 a, df64 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
+TCG_FN bool operator>=(df64 a, df64 b) { return b <= a; }
+TCG_FN bool operator==(df64 a, df64 b) { return a.hi == b.hi && a.lo == b.lo; }
+TCG_FN bool operator!=(df64 a, df64 b) { return !(a == b); }
+
+// ------------------------------------------------------------------ functions
+TCG_FN df64 m_abs(df64 a) { return (a.hi < 0.0f) ? -a : a; }
+TCG_FN df64 m_max(df64 a, df64 b) { return (a < b) ? b : a; }
+TCG_FN df64 m_min(df64 a, df64 b) { return (b < a) ? b : a; }
+
+TCG_FN df64 m_sqrt(df64 a) {
+  if (!(a.hi > 0.0f)) return df64::make(sqrtf(a.hi), 0.0f);  // 0, or NaN below 0
+  const float s = sqrtf(a.hi);
+  float p, e;
+  two_prod(s, s, p, e);
+  // (a - s^2) / (2 s) with a - s^2 formed exactly to first order (a.hi - p is exact)
+  const float r = df_add_rn(df_sub_rn(df_sub_rn(a.hi, p), e), a.lo);
+  const float c = df_mul_rn(r, df_mul_rn(0.5f, df_rcp(s)));
+  float h, l;
+  fast_two_sum(s, c, h, l);
+  return df64::make(h, l);
+}
+
+// 2^(j/16), j = 0..15, split into leading and trailing FP32 parts at compile time.
+#define TCG_DF_EXP2(v) {float(v), float((v) - double(float(v)))}
+#define TCG_DF_EXP2_TABLE                                                                                \
+  {TCG_DF_EXP2(1.0), TCG_DF_EXP2(1.0442737824274138), TCG_DF_EXP2(1.0905077326652577),               \
+   TCG_DF_EXP2(1.1387886347566916), TCG_DF_EXP2(1.189207115002721), TCG_DF_EXP2(1.241857812073484),   \
+   TCG_DF_EXP2(1.2968395546510096), TCG_DF_EXP2(1.3542555469368927), TCG_DF_EXP2(1.4142135623730951), \
+   TCG_DF_EXP2(1.4768261459394993), TCG_DF_EXP2(1.5422108254079407), TCG_DF_EXP2(1.6104903319492543), \
+   TCG_DF_EXP2(1.681792830507429), TCG_DF_EXP2(1.7562521603732995), TCG_DF_EXP2(1.8340080864093424),  \
+   TCG_DF_EXP2(1.9152065613971474)}
+static __device__ const float2 kDfExp2Dev[16] = TCG_DF_EXP2_TABLE;
+static const float2 kDfExp2Host[16] = TCG_DF_EXP2_TABLE;
+
+// exp(x) for a df64 argument (method in the header comment).
+__host__ __device__ __noinline__ inline df64 m_exp(df64 x) {
+  if (x.hi < -87.0f) return df64::make(0.0f, 0.0f);
+  if (x.hi > 80.0f) x = df64::make(80.0f, 0.0f);
+  if (!(x.hi == x.hi)) return x;  // NaN
+  // ln2/16 = C1 + C2 + C3 (C1 = 0x1.62ep-5, 12 significant bits)
+  constexpr float C1 = 0.043319702148437500f;
+  constexpr float C2 = 1.9966365e-06f;
+  constexpr float C3 = 1.02912186e-13f;
+  constexpr float INV = 23.083120654223414f;  // 16 / ln 2
+  const float kf = rintf(x.hi * INV);
+  const int k = (int)kf;
+  // r = x - k ln2/16: x.hi - k C1 is exact (k C1 is exact, and within a factor 2 of x.hi)
+  const float a = df_sub_rn(x.hi, df_mul_rn(kf, C1));
+  df64 r;
+  {
+    float s, e;
+    two_sum(a, x.lo, s, e);
+    float p, pe;
+    two_prod(kf, C2, p, pe);
+    float s2, e2;
+    two_sum(s, -p, s2, e2);
+    e = df_add_rn(df_add_rn(e, e2), df_sub_rn(-pe, df_mul_rn(kf, C3)));
+    float h, l;
+    fast_two_sum(s2, e, h, l);
+    r = df64::make(h, l);
+  }
+  // exp(r) - 1 = r + r^2/2 + r^3/6 + r^4 (1/24 + r/120 + r^2/720); the last group is
+  // below 1e-8 and needs only FP32
+  const df64 r2 = r * r;
+  const df64 r3 = r2 * r;
+  const float rh = r.hi;
+  float q = df_fma(rh, 1.0f / 720.0f, 1.0f / 120.0f);
+  q = df_fma(rh, q, 1.0f / 24.0f);
+  q = df_mul_rn(df_mul_rn(r2.hi, r2.hi), q);
+  df64 em1 = r + df64::make(0.5f * r2.hi, 0.5f * r2.lo);
+  em1 = em1 + r3 * df64(1.0 / 6.0);
+  em1 = add_f(em1, q);
+  // exp(x) = 2^m 2^(j/16) (1 + em1) with k = 16 m + j
+  const int j = k & 15;
+  const int m = (k - j) / 16;
+#ifdef __CUDA_ARCH__
+  const float2 t = __ldg(&kDfExp2Dev[j]);
+#else
+  const float2 t = kDfExp2Host[j];
+#endif
+  const df64 tj = df64::make(t.x, t.y);
+  const df64 y = tj + tj * em1;
+  const float sc = df_pow2i(m);
+  return df64::make(y.hi * sc, y.lo * sc);
+}
+
+// log(x) for a df64 argument (method in the header comment).
+__host__ __device__ __noinline__ inline df64 m_log(df64 x) {
+  if (!(x.hi > 0.0f)) {
+    if (x.hi == 0.0f) return df64::make(float(-DF_BIG), 0.0f);
+    return df64::make(logf(x.hi), 0.0f);  // NaN
+  }
+  const float y0 = logf(x.hi);
+  const df64 d = add_f(x * m_exp(df64::make(-y0, 0.0f)), -1.0f);
+  const float dh = d.hi;
+  const float corr = df_mul_rn(df_mul_rn(dh, dh), df_fma(dh, 1.0f / 3.0f, -0.5f));
+  return add_f(df64::make(y0, 0.0f) + d, corr);
+}
+
+}  // namespace tcg

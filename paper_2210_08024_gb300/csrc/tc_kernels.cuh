@@ -226,19 +226,35 @@ TCG_FN void substep_paper(const CellC<double>& c, const DevParams& p, double dt,
 }
 
 // ------------------------------------------------------------------ mode 1: coupled Newton, FP64
-// f(y) = (H/K, C_H2, C_H+) at T = mu^n y0 with the C/O/e equilibrium and T_d re-solved.
-// `qout`, when given, receives the C/O/e equilibrium of the evaluation.
+// f(y) = (H/K, C_H2, C_H+) at T = mu^n y0 with the C/O/e equilibrium and T_d re-solved,
+// the source terms in precision F (double: the FP64 solves; df64: the high-precision
+// evaluations of the mixed solve), the state and f in FP64.  `qout`, when given,
+// receives the C/O/e equilibrium of the evaluation.
+template <class F>
+TCG_FN void feval_t(const CellC<F>& c, const ChemT<F>& b, const CoolT<F>& k, double y1, double y2, double Kinv,
+                    F& xe_guess, F& td_guess, double* f, Equil<F>* qout = nullptr) {
+  Equil<F> q = equilibrium(c, b, F(y1), F(y2), xe_guess);
+  if (qout) *qout = q;
+  Src<F> s = source(c, b, k, F(y1), F(y2), F(1.0 - 2.0 * y1 - y2), q, F(-1.0), td_guess);
+  xe_guess = q.xe;
+  td_guess = s.Td;
+  f[0] = double(s.H) * Kinv;
+  f[1] = double(s.CH2);
+  f[2] = double(s.CHp);
+}
 TCG_FN void feval64(const CellC<double>& c, const ChemT<double>& b, const CoolT<double>& k, double y1,
                     double y2, double Kinv, double& xe_guess, double& td_guess, double* f,
                     Equil<double>* qout = nullptr) {
-  Equil<double> q = equilibrium(c, b, y1, y2, xe_guess);
-  if (qout) *qout = q;
-  Src<double> s = source(c, b, k, y1, y2, 1.0 - 2.0 * y1 - y2, q, -1.0, td_guess);
-  xe_guess = q.xe;
-  td_guess = s.Td;
-  f[0] = s.H * Kinv;
-  f[1] = s.CH2;
-  f[2] = s.CHp;
+  feval_t<double>(c, b, k, y1, y2, Kinv, xe_guess, td_guess, f, qout);
+}
+
+// The FP64 fields of a C/O/e equilibrium solved in precision F.
+template <class F>
+TCG_FN Equil<double> equil64(const Equil<F>& q) {
+  Equil<double> r;
+  r.xe = double(q.xe); r.xCp = double(q.xCp); r.xCO = double(q.xCO); r.xC = double(q.xC);
+  r.xO = double(q.xO); r.xOp = double(q.xOp); r.xMHp = double(q.xMHp);
+  return r;
 }
 
 // Gaussian elimination with partial pivoting on a 3x3 system, in the precision F of its
@@ -742,14 +758,20 @@ TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double d
   finish_substep_q(c, p, dt, dts, last, y, qb, s);
 }
 
-// Substep length of Sec. 6.1 from the FP64 source terms at the substep start; `src`,
-// when given, receives those terms (H, C_H2, C_H+).
+// Substep length of Sec. 6.1 from the source terms at the substep start, evaluated in
+// precision F (FP64, or df64 in the mixed modes); K is the cell's FP64 heat-capacity
+// factor.  `src`, when given, receives those terms (H, C_H2, C_H+).
+template <class F>
+TCG_FN double substep_start_t(const CellC<F>& cc, double K, const DevParams& p, double dt, const LaneState& s,
+                              F& td_g, bool& last, double* src = nullptr) {
+  double H0, CH2, CHp;
+  start_sources<F>(cc, p, s, td_g, H0, CH2, CHp);
+  if (src) { src[0] = H0; src[1] = CH2; src[2] = CHp; }
+  return substep_len(p, dt - s.t, K * s.Tmu, H0, CH2, CHp, last);
+}
 TCG_FN double substep_start64(const CellC<double>& c, const DevParams& p, double dt, const LaneState& s,
                               double& td_g, bool& last, double* src = nullptr) {
-  double H0, CH2, CHp;
-  start_sources<double>(c, p, s, td_g, H0, CH2, CHp);
-  if (src) { src[0] = H0; src[1] = CH2; src[2] = CHp; }
-  return substep_len(p, dt - s.t, c.K * s.Tmu, H0, CH2, CHp, last);
+  return substep_start_t<double>(c, c.K, p, dt, s, td_g, last, src);
 }
 
 template <int LPC = 1>
@@ -869,11 +891,14 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
   return -1;
 }
 
-// FP64 polish of the mixed iteration's root: chord corrections with the residual
-// evaluated entirely in FP64 and the last (FP32-built) Jacobian.  The FP32 root is off
-// the FP64 one by the FP32 rounding floor of f (~1e-6 relative in T near stiff
-// equilibria, where H is a small difference of large terms), and the scheme can
-// amplify such errors a hundredfold over a step, so every substep is polished.
+// High-precision polish of the mixed iteration's root: chord corrections with the
+// residual's source terms evaluated in df64 (double-float, ~1e-12 relative on the
+// terms, tc_df64.cuh) and the last (FP32-built) Jacobian.  The FP32 root is off the FP64
+// one by the FP32 rounding floor of f (~1e-6 relative in T near stiff equilibria, where
+// H is a small difference of large terms), and the scheme can amplify such errors a
+// hundredfold over a step, so every substep is polished.  With F = double the same
+// polish runs in FP64; df64 gives the same roots to ~1e-11 relative (the terms' errors
+// divided by the logarithmic slope of H in T) at a fraction of the FP64 pipe's time.
 // The Jacobian is the FP32 forward difference built at the FP32 root (fd_jacobian32).
 // A chord iteration contracts by the Jacobian's relative error rho (~1e-3 there), so
 // after a correction d_k the remaining error is about rho d_k / (1 - rho), with rho
@@ -881,20 +906,21 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
 // (abundances relative to max(x, 1e-4)), or when a single correction is below 1e-7;
 // after at most five corrections, otherwise the FP64 solver takes the substep.
 // Measured on 4 x 4096 random-state cells, largest error in T against the FP64 oracle
-// after one step, and FP64 polish evaluations per slab substep:
+// after one step, and polish evaluations per slab substep:
 //   Jacobian from the FP32 iteration, single correction below 1e-8: 4.6e-6, 1.83
 //   (below 1e-7: 1.05e-5, 1.13, over the bound);
 //   Jacobian rebuilt at the FP32 root, single correction below 1e-7: 1.1e-6, 1.14.
-// `qlast` receives the C/O/e equilibrium of the last FP64 evaluation.
-TCG_FN bool polish64(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
-                     double dts, double* y, const double J[3][3], double& xe_g, double& td_g, Equil<double>& qlast) {
+// `qlast` receives the C/O/e equilibrium of the last evaluation.
+template <class F>
+TCG_FN bool polish_hp(const CellC<F>& c, const DevParams& p, double mu, double Kinv, const double* yn, double dts,
+                      double* y, const double J[3][3], F& xe_g, F& td_g, Equil<F>& qlast) {
   double prev = -1.0;
   for (int it = 0; it < 5; ++it) {
     TCG_COUNT_D(polish_it);
-    ChemT<double> b = chem_T(c, mu * y[0], p.flags);
-    CoolT<double> k = cool_T(c, b, p.flags);
+    ChemT<F> b = chem_T(c, F(mu * y[0]), p.flags);
+    CoolT<F> k = cool_T(c, b, p.flags);
     double f0[3];
-    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, &qlast);
+    feval_t<F>(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, &qlast);
     // FP64 residual; the correction (below ~1e-6 relative) solved in FP32 with the FP32
     // Jacobian, whose own error (~1e-3) sets the contraction
     float Jw[3][3], rhs[3], d32[3];
@@ -923,18 +949,19 @@ TCG_FN bool polish64(const CellC<double>& c, const DevParams& p, double mu, doub
   return false;
 }
 
-// One mixed-precision substep.  FP64 work: the source terms at the substep start that
-// set its length (Sec. 6.1; the length decides where the trajectory is sampled: FP32
-// heating and cooling sums are off by up to ~5e-5 relative, and a length that far off
-// moved hot cells cooling through the Lyman-alpha peak by 1e-3 in T after ~70
-// substeps), and the polish of the root, whose last evaluation also gives the C/O/e
-// equilibrium that sets mu at the end (finish_substep_q).  FP32 work: every Newton iteration before
-// the polish and the Jacobian.  The solve starts from `seed` when given, else from the
+// One mixed-precision substep.  High-precision work, in df64: the source terms at the
+// substep start that set its length (Sec. 6.1; the length decides where the trajectory
+// is sampled: FP32 heating and cooling sums are off by up to ~5e-5 relative, and a
+// length that far off moved hot cells cooling through the Lyman-alpha peak by 1e-3 in T
+// after ~70 substeps), and the polish of the root, whose last evaluation also gives the
+// C/O/e equilibrium that sets mu at the end (finish_substep_q).  FP32 work: every Newton
+// iteration before the polish and the Jacobian.  FP64 work: the Newton updates and
+// residuals, and the fallback.  The solve starts from `seed` when given, else from the
 // start state.
 template <int LPC = 1>
-TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<float>& cf, const DevParams& p, double dt,
-                                double dts, bool last, LaneState& s, float& xe_g, float& td_g, double td64,
-                                const double* seed) {
+TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<df64>& cd, const CellC<float>& cf,
+                                const DevParams& p, double dt, double dts, bool last, LaneState& s, float& xe_g,
+                                float& td_g, const df64& td_hp, const double* seed) {
   const double yn[3] = {s.Tmu, s.xH2, s.xHp};
   const double Kinv = 1.0 / c.K;
   double y[3] = {yn[0], yn[1], yn[2]};
@@ -951,31 +978,31 @@ TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<float>& cf, 
     y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2];
     it = newton_mixed<LPC>(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, J, polish);
   }
-  Equil<double> qlast;
+  Equil<df64> qlast;
   if (it >= 0) {
     if (polish) s.status |= ST_POLISH;
     fd_jacobian32<LPC>(cf, p, s.mu, Kinv, dts, y, xe_g, td_g, J);
-    double xg = double(xe_g), tg = double(td_g);
-    if (!polish64(c, p, s.mu, Kinv, yn, dts, y, J, xg, tg, qlast)) it = -1;
+    df64 xg = df64::make(xe_g, 0.0f), tg = df64::make(td_g, 0.0f);
+    if (!polish_hp<df64>(cd, p, s.mu, Kinv, yn, dts, y, J, xg, tg, qlast)) it = -1;
   }
   if (it < 0) {
     // The plain FP64 solver finishes this substep (same length, same start state).
     s.status |= ST_FALLBACK;
-    double xg = s.xe, tg = td64;
+    double xg = s.xe, tg = double(td_hp);
     solve_substep64<LPC>(c, p, dt, dts, last, s, xg, tg);
   } else {
     s.iters += it;
-    finish_substep_q(c, p, dt, dts, last, y, qlast, s);
+    finish_substep_q(c, p, dt, dts, last, y, equil64(qlast), s);
   }
   xe_g = float(s.xe);
 }
 
 template <int LPC = 1>
-TCG_FN void substep_mixed(const CellC<double>& c, const CellC<float>& cf, const DevParams& p, double dt,
-                          LaneState& s, float& xe_g, float& td_g, double& td64) {
+TCG_FN void substep_mixed(const CellC<double>& c, const CellC<df64>& cd, const CellC<float>& cf, const DevParams& p,
+                          double dt, LaneState& s, float& xe_g, float& td_g, df64& td_hp) {
   bool last;
-  const double dts = substep_start64(c, p, dt, s, td64, last);
-  substep_mixed_solve<LPC>(c, cf, p, dt, dts, last, s, xe_g, td_g, td64, nullptr);
+  const double dts = substep_start_t<df64>(cd, c.K, p, dt, s, td_hp, last);
+  substep_mixed_solve<LPC>(c, cd, cf, p, dt, dts, last, s, xe_g, td_g, td_hp, nullptr);
 }
 
 // ------------------------------------------------------------------ seeding (modes 3, 4)
@@ -1047,10 +1074,11 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
   float lf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   LaneState s;
   CellC<double> c;
-  CellC<float> cf;   // FP32 copy of the cell constants (mixed modes)
+  CellC<float> cf;   // FP32 copy of the cell constants (mixed and seeded modes)
+  CellC<df64> cd;    // df64 copy (mixed modes: substep-start sources and polish)
   double xe_g = -1.0, td_g = -1.0;
   float xe_gf = -1.f, td_gf = -1.f;
-  double td64 = -1.0;
+  df64 td_hp = df64(-1.0);   // dust-temperature guess of the df64 evaluations
   DevFields fb;
   long long li = -1;   // local cell index within its box
   bool have = false;
@@ -1094,7 +1122,10 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
           cf = cast_cell<float>(c);
           xe_gf = float(s.xe);
           td_gf = -1.f;
-          td64 = -1.0;
+        }
+        if constexpr (MIXED) {
+          cd = cast_cell<df64>(c);
+          td_hp = df64(-1.0);
         }
         if constexpr (SEEDED) {
           const double chi_fuv = (1.8e-4 * fb.chi_pe[li] + 3.0e-5 * fb.chi_lw[li]) / 2.1e-4;
@@ -1122,7 +1153,8 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
           s.status |= ST_MAX_SUB;
           s.t = dt;
         } else {
-          dts = substep_start64(c, p, dt, s, (MODE == 3) ? td64 : td_g, last, src);
+          if constexpr (MODE == 3) dts = substep_start_t<df64>(cd, c.K, p, dt, s, td_hp, last, src);
+          else dts = substep_start64(c, p, dt, s, td_g, last, src);
           need = true;
         }
       }
@@ -1133,7 +1165,8 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
       if (need) {
         double seed[3];
         const bool ok = seed_from_outputs(o, g, s, p, seed);
-        if constexpr (MODE == 3) substep_mixed_solve(c, cf, p, dt, dts, last, s, xe_gf, td_gf, td64, ok ? seed : nullptr);
+        if constexpr (MODE == 3)
+          substep_mixed_solve(c, cd, cf, p, dt, dts, last, s, xe_gf, td_gf, td_hp, ok ? seed : nullptr);
         else solve_substep64(c, p, dt, dts, last, s, xe_g, td_g, ok ? seed : nullptr, &cf);
         if (!finite3(s.Tmu, s.xH2, s.xHp)) {
           s.status |= ST_NONFIN;
@@ -1151,7 +1184,7 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
         } else if constexpr (MODE == 1) {
           substep_newton64<LPC>(c, p, dt, s, xe_g, td_g);
         } else if constexpr (MODE == 2) {
-          substep_mixed<LPC>(c, cf, p, dt, s, xe_gf, td_gf, td64);
+          substep_mixed<LPC>(c, cd, cf, p, dt, s, xe_gf, td_gf, td_hp);
         }
         if (!finite3(s.Tmu, s.xH2, s.xHp)) {
           s.status |= ST_NONFIN;

@@ -6,6 +6,10 @@
 #include "../../include/tc.h"
 #include "../../include/tc_peak.h"
 
+namespace tcg {
+int df64_peak_launch(int kind, int grid, int block, int iters, double* sink, void* stream);  // tc_df64_diag.cu
+}
+
 namespace {
 constexpr int CH = 8;
 
@@ -64,6 +68,8 @@ extern "C" int tc_peak_launch(int kind, int grid, int block, int iters, double* 
     case 6: k_peak<6><<<grid, block, 0, st>>>(iters, sink); break;
     case 7: k_peak<7><<<grid, block, 0, st>>>(iters, sink); break;
     case 8: k_peak<8><<<grid, block, 0, st>>>(iters, sink); break;
+    case 9:
+    case 10: return tcg::df64_peak_launch(kind, grid, block, iters, sink, stream);
     default: return TC_EINVAL;
   }
   return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ECUDA;

@@ -8,7 +8,8 @@
 //   CoolT<F>   temperature-only pieces of the heating and cooling functions.
 // Powers of T and psi are taken as exp(c ln T), exp(c ln psi) from one logarithm.
 //
-// F is double for the FP64 paths and float for the mixed path's source terms.  Terms
+// F is double for the FP64 paths, float for the mixed path's Newton iterations and df64
+// (double-float, tc_df64.cuh) for its high-precision evaluations.  Terms
 // the paper names but does not print (closures: cited fits and tables it does not
 // reproduce) use one stated definition each, labelled where it is a stand-in for the
 // cited source; the CPU checker uses the same definitions, written independently.
@@ -16,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include "tc_df64.cuh"
 
 // Physics and substep functions are host+device so the host compiler can also build
 // them (used by the host-side test harness of the library's own kernels).
@@ -66,6 +69,27 @@ TCG_FN double m_min(double a, double b) { return fmin(a, b); }
 TCG_FN float m_min(float a, float b) { return fminf(a, b); }
 TCG_FN double m_abs(double a) { return fabs(a); }
 TCG_FN float m_abs(float a) { return fabsf(a); }
+
+// Precision traits of the scalar types: the relative tolerance of the inner root solves
+// (C/O/e equilibrium, dust temperature), a little above each type's rounding; whether
+// the type has only FP32's exponent range; and its class for the work counter
+// (0 FP64, 1 FP32, 2 df64).
+template <class F> struct Prec;
+template <> struct Prec<double> {
+  static constexpr double root_tol = 1e-14;
+  static constexpr bool fp32_range = false;
+  static constexpr int cls = 0;
+};
+template <> struct Prec<float> {
+  static constexpr double root_tol = 1e-7;
+  static constexpr bool fp32_range = true;
+  static constexpr int cls = 1;
+};
+template <> struct Prec<df64> {
+  static constexpr double root_tol = 1e-12;
+  static constexpr bool fp32_range = true;
+  static constexpr int cls = 2;
+};
 
 template <class F> TCG_FN F logistic(F z) { return F(1) / (F(1) + m_exp(-z)); }
 
@@ -326,7 +350,7 @@ template <class F> struct Equil {
 // Electron balance g(x_e) = x_e - a0 - w x_C+(x_e) = 0 (Eqs. e:xEL / e:xELhot blended by
 // S(T), Eq. eq:C+_frac for x_C+), solved by Newton's method with the analytic derivative
 // inside the bracket [a0, a0 + w x_C,tot] (bisection when a step leaves it), warm-started
-// at `guess`, to a relative step of 1e-14 (FP64) / 1e-7 (FP32).
+// at `guess`, to a relative step of Prec<F>::root_tol.
 template <class F> TCG_BIG Equil<F> equilibrium(const CellC<F>& c, const ChemT<F>& b, F xH2,
                                                                   F xHp, F guess) {
   TCG_COUNT(equil);
@@ -364,7 +388,7 @@ template <class F> TCG_BIG Equil<F> equilibrium(const CellC<F>& c, const ChemT<F
     xe = a0;
   } else {
     F x = (guess > lo && guess < hi) ? guess : hi;
-    const F tol = (sizeof(F) == 8) ? F(1e-14) : F(1e-7);
+    const F tol = F(Prec<F>::root_tol);
     xe = x;
     for (int it = 0; it < 100; ++it) {
       TCG_COUNT(equil_it);
@@ -411,7 +435,7 @@ template <class F> TCG_FN F dust_T(const CellC<F>& c, F T, F sqT, F guess) {
     y = m_exp(m_log((c.Gd + C * T) / c.Bd) * F(1.0 / 6.0));
     if (!(y > lo && y < hi)) y = F(0.5) * (lo + hi);
   }
-  const F tol = (sizeof(F) == 8) ? F(1e-14) : F(1e-7);
+  const F tol = F(Prec<F>::root_tol);
   for (int it = 0; it < 100; ++it) {
     TCG_COUNT(dust_it);
     F y2 = y * y;
@@ -502,10 +526,11 @@ template <class F> TCG_BIG Src<F> source(const CellC<F>& c, const ChemT<F>& b, c
   {
     F nL = n * k.rvLlow;                                                // H2 ro-vibrational
     F den = nL + k.rvLLTE;
-    // harmonic combination L_LTE n L_low / (n L_low + L_LTE); in FP32 the product of the
-    // two rates (~1e-22 x 1e-24) underflows, so the ratio is taken first there.
+    // harmonic combination L_LTE n L_low / (n L_low + L_LTE); in FP32's exponent range
+    // the product of the two rates (~1e-22 x 1e-24) underflows, so the ratio is taken
+    // first there.
     F Lrv;
-    if constexpr (sizeof(F) == 4) Lrv = k.rvLLTE * (nL / den);
+    if constexpr (Prec<F>::fp32_range) Lrv = k.rvLLTE * (nL / den);
     else Lrv = k.rvLLTE * nL / den;
     Lhyd += (den > F(0)) ? xH2 * Lrv / n : F(0);
   }

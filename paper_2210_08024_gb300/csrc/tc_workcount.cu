@@ -1,7 +1,7 @@
 // Host program that counts the FP64 arithmetic of the step as the library performs it
 // (not part of libtc_gb300.so; built and run by paper_2210_08024_gb300/work.py).
 //
-// Two passes:
+// Two passes (FP64, FP32 and df64 calls counted separately):
 //  1. cost per call: each building block of the step (the two temperature blocks, one
 //     C/O/e root iteration and its set-up, one dust-temperature iteration and its
 //     set-up, the source terms) is instantiated with a counting scalar and evaluated
@@ -25,14 +25,14 @@ struct Calls {
   long long chem_T, cool_T, equil, equil_it, dust, dust_it, source;
   long long newton64_it, chord64_it, newton32_it, polish_it, substep_paper, picard_it;
 };
-Calls calls[2];  // [0] FP64, [1] FP32
+Calls calls[3];  // [0] FP64, [1] FP32, [2] df64 (double-float)
 }  // namespace wc
 
 #ifdef __CUDA_ARCH__
 #define TCG_COUNT(name)
 #define TCG_COUNT_D(name)
 #else
-#define TCG_COUNT(name) (::wc::calls[sizeof(F) == 4 ? 1 : 0].name++)
+#define TCG_COUNT(name) (::wc::calls[::tcg::Prec<F>::cls].name++)
 #define TCG_COUNT_D(name) (::wc::calls[0].name++)
 #endif
 
@@ -51,6 +51,11 @@ struct CntD {
   constexpr CntD(double x) : v(x) {}
 };
 static_assert(sizeof(CntD) == 8, "counting scalar must look like a double");
+template <> struct Prec<CntD> {
+  static constexpr double root_tol = 1e-14;
+  static constexpr bool fp32_range = false;
+  static constexpr int cls = 0;
+};
 inline CntD operator+(CntD a, CntD b) { ++g_ops.add; return CntD(a.v + b.v); }
 inline CntD operator-(CntD a, CntD b) { ++g_ops.add; return CntD(a.v - b.v); }
 inline CntD operator*(CntD a, CntD b) { ++g_ops.mul; return CntD(a.v * b.v); }
@@ -169,11 +174,13 @@ int main(int argc, char** argv) {
   for (int mode = 0; mode <= 2; ++mode) {
     wc::calls[0] = wc::Calls{};
     wc::calls[1] = wc::Calls{};
+    wc::calls[2] = wc::Calls{};
     long long nsub = 0;
     for (int64_t i = 0; i < n; ++i) {
       CellC<double> c = make_cell(col(0)[i], col(1)[i], col(2)[i], col(3)[i], col(4)[i], col(5)[i], col(6)[i],
                                   col(7)[i], col(8)[i], p);
       CellC<float> cf = cast_cell<float>(c);
+      CellC<df64> cd = cast_cell<df64>(c);
       LaneState s;
       s.t = 0; s.xH2 = col(10)[i]; s.xHp = col(11)[i]; s.Td = -1; s.nsub = 0; s.status = 0; s.iters = 0;
       ChemT<double> b0 = chem_T(c, col(9)[i], p.flags);
@@ -181,29 +188,37 @@ int main(int argc, char** argv) {
       s.xe = q0.xe; s.xCp = q0.xCp; s.xCO = q0.xCO;
       s.mu = c.muH / (1.1 + s.xe - s.xH2);
       s.Tmu = col(9)[i] / s.mu;
-      double xg = s.xe, tg = -1.0, td64 = -1.0;
+      double xg = s.xe, tg = -1.0;
+      df64 thp = df64(-1.0);
       float xgf = (float)s.xe, tgf = -1.f;
       while (s.t < dt && s.nsub < p.max_sub) {
         if (mode == 0) substep_paper(c, p, dt, s);
         else if (mode == 1) substep_newton64(c, p, dt, s, xg, tg);
-        else substep_mixed(c, cf, p, dt, s, xgf, tgf, td64);
+        else substep_mixed(c, cd, cf, p, dt, s, xgf, tgf, thp);
         if (!finite3(s.Tmu, s.xH2, s.xHp)) break;
       }
       nsub += s.nsub;
     }
     const wc::Calls& k = wc::calls[0];
     const wc::Calls& f = wc::calls[1];
+    const wc::Calls& h = wc::calls[2];
     printf("  \"mode%d\": {\"substeps\": %.4f, \"fp64\": {\"chem_T\": %.4f, \"cool_T\": %.4f, \"equil\": %.4f, "
            "\"equil_it\": %.4f, \"dust\": %.4f, \"dust_it\": %.4f, \"source\": %.4f, \"newton64_it\": %.4f, "
            "\"chord64_it\": %.4f, \"newton32_it\": %.4f, \"polish_it\": %.4f, \"substep_paper\": %.4f, "
-           "\"picard_it\": %.4f}, \"fp32\": {\"chem_T\": %.4f, \"cool_T\": %.4f, \"equil\": %.4f, "
-           "\"equil_it\": %.4f, \"dust\": %.4f, \"dust_it\": %.4f, \"source\": %.4f}}%s\n",
+           "\"picard_it\": %.4f}, ",
            mode, (double)nsub / n, (double)k.chem_T / n, (double)k.cool_T / n, (double)k.equil / n,
            (double)k.equil_it / n, (double)k.dust / n, (double)k.dust_it / n, (double)k.source / n,
            (double)k.newton64_it / n, (double)k.chord64_it / n, (double)k.newton32_it / n, (double)k.polish_it / n,
-           (double)k.substep_paper / n, (double)k.picard_it / n, (double)f.chem_T / n, (double)f.cool_T / n,
-           (double)f.equil / n, (double)f.equil_it / n, (double)f.dust / n, (double)f.dust_it / n,
-           (double)f.source / n, mode < 2 ? "," : "");
+           (double)k.substep_paper / n, (double)k.picard_it / n);
+    for (int cl = 1; cl <= 2; ++cl) {
+      const wc::Calls& x = (cl == 1) ? f : h;
+      printf("\"%s\": {\"chem_T\": %.4f, \"cool_T\": %.4f, \"equil\": %.4f, \"equil_it\": %.4f, \"dust\": %.4f, "
+             "\"dust_it\": %.4f, \"source\": %.4f}%s",
+             (cl == 1) ? "fp32" : "df64", (double)x.chem_T / n, (double)x.cool_T / n, (double)x.equil / n,
+             (double)x.equil_it / n, (double)x.dust / n, (double)x.dust_it / n, (double)x.source / n,
+             (cl == 1) ? ", " : "");
+    }
+    printf("}%s\n", mode < 2 ? "," : "");
   }
   printf("}\n");
   return 0;

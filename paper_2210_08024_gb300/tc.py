@@ -140,6 +140,8 @@ def _load():
     L.tc_peak_launch.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                  ctypes.c_void_p]
     L.tc_peak_chains.restype = ctypes.c_int
+    L.tc_df64_eval.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
+                               ctypes.c_void_p]
     L.tc_step_host_static.argtypes = [ctypes.POINTER(tc_params), ctypes.POINTER(tc_fields), ctypes.c_double,
                                       ctypes.c_void_p]
     # seed network (include/tc_mlp.h)
@@ -327,6 +329,17 @@ def tc_peak_launch(kind: int, grid: int, block: int, iters: int, sink, stream=No
 
 def tc_peak_chains() -> int:
     return int(lib.tc_peak_chains())
+
+
+DF64_OPS = {"add": 0, "mul": 1, "div": 2, "sqrt": 3, "exp": 4, "log": 5}
+
+
+def tc_df64_eval(op: str, a, b, out, stream=None) -> None:
+    """Element-wise df64 arithmetic on the device (include/tc_peak.h): a, b, out are
+    contiguous CUDA float64 tensors of one size (b only for add, mul and div)."""
+    n = out.numel()
+    _check(lib.tc_df64_eval(DF64_OPS[op], a.data_ptr(), b.data_ptr() if b is not None else None, out.data_ptr(),
+                            n, _stream_ptr(stream)), "tc_df64_eval")
 
 
 # ----------------------------------------------------------------------------- helpers

@@ -18,6 +18,12 @@ scalar type; its counts per iteration are stated here from the code:
     paper-scheme substep    18 add, 18 mul,  8 div   (FD slope, T update, 2x2 solve)
     predictor sweep         30 add, 30 mul,  8 div   (2x2 closed form, T step, change)
 
+The mixed mode's high-precision evaluations run in df64 (double-float, csrc/tc_df64.cuh)
+on the FP32 pipes.  Their operations by class are counted the same way ("mode2_df64");
+each costs this many FP32-pipe instructions, counted from tc_df64.cuh (error-free
+transformations included; exp and log with their call overhead):
+    add 11, mul 7, div 28, sqrt 20, exp 125, log 170
+
     python -m paper_2210_08024_gb300.work
 """
 from __future__ import annotations
@@ -45,6 +51,7 @@ LINALG = {
     "substep_paper": {"add": 18, "mul": 18, "div": 8},
     "picard_it": {"add": 30, "mul": 30, "div": 8},
 }
+DF64_FP32_INST = {"add": 11, "mul": 7, "div": 28, "sqrt": 20, "exp": 125, "log": 170}
 CLASSES = ("add", "mul", "div", "sqrt", "exp", "log")
 BLOCKS = {"chem_T": "cost_chem_T", "cool_T": "cost_cool_T", "source": "cost_source", "equil": "cost_equil_setup",
           "equil_it": "cost_equil_iter", "dust": "cost_dust_setup", "dust_it": "cost_dust_iter"}
@@ -74,28 +81,34 @@ def _ops(calls: dict, counts: dict, linalg: bool) -> dict:
 def per_cell(counts: dict) -> dict:
     """FP64 operations per cell by class for each mode; for the mixed mode also its FP32
     operations ("mode2_fp32": the same building blocks instantiated in FP32, whose
-    exp, log, sqrt and divide the fast-math build issues to the MUFU pipe)."""
+    exp, log, sqrt and divide the fast-math build issues to the MUFU pipe) and its df64
+    operations ("mode2_df64", with "fp32_inst": their FP32-pipe instructions)."""
     out = {}
     for mode in ("mode0", "mode1", "mode2"):
         out[mode] = _ops(counts[mode]["fp64"], counts, True)
         out[mode]["substeps"] = counts[mode]["substeps"]
     out["mode2_fp32"] = _ops(counts["mode2"]["fp32"], counts, False)
+    hp = _ops(counts["mode2"].get("df64", {}), counts, False)
+    hp["fp32_inst"] = round(sum(hp[c] * DF64_FP32_INST[c] for c in CLASSES), 1)
+    out["mode2_df64"] = hp
     return out
 
 
 def algorithmic(counts: dict) -> dict:
     """The method's own work knobs per slab cell: substeps, evaluations of the source
-    terms f (FP64 and FP32), and Newton-type iterations per substep."""
+    terms f (FP64, FP32 and df64 together, and the FP64 ones alone), Newton-type
+    iterations per substep and polish corrections per substep."""
     out = {}
     for mode in ("mode0", "mode1", "mode2"):
-        k, f = counts[mode]["fp64"], counts[mode]["fp32"]
+        k, f, h = counts[mode]["fp64"], counts[mode]["fp32"], counts[mode].get("df64", {})
         ns = counts[mode]["substeps"]
-        src = k["source"] + f["source"]
+        src = k["source"] + f["source"] + h.get("source", 0.0)
         its = k["newton64_it"] + k["chord64_it"] + k["newton32_it"]
         out[mode] = {"substeps": round(ns, 4), "source_evals": round(src, 3),
                      "source_evals_per_substep": round(src / ns, 3) if ns else 0.0,
+                     "fp64_source_evals": round(k["source"], 3),
                      "iterations_per_substep": round(its / ns, 3) if ns else 0.0,
-                     "fp64_polish_per_substep": round(k["polish_it"] / ns, 3) if ns else 0.0}
+                     "polish_per_substep": round(k["polish_it"] / ns, 3) if ns else 0.0}
     return out
 
 

@@ -70,8 +70,10 @@ int main(int argc, char** argv) {
     ChemT<double> b0 = chem_T(c, T0, p.flags);
     Equil<double> q0 = equilibrium(c, b0, x20, xp0, -1.0);
     s.xe = q0.xe; s.xCp = q0.xCp; s.xCO = q0.xCO;
-    double xe_g = q0.xe, td_g = -1.0, td64 = -1.0;
+    double xe_g = q0.xe, td_g = -1.0;
     CellC<float> cf = cast_cell<float>(c);
+    CellC<df64> cd = cast_cell<df64>(c);
+    df64 td_hp = df64(-1.0);
     float xe_gf = float(s.xe), td_gf = -1.f;
     s.mu = c.muH / (1.1 + s.xe - x20);
     s.Tmu = T0 / s.mu;
@@ -83,7 +85,7 @@ int main(int argc, char** argv) {
       }
       if (mode == 0) substep_paper(c, p, dt, s);
       else if (mode == 1) substep_newton64(c, p, dt, s, xe_g, td_g);
-      else substep_mixed(c, cf, p, dt, s, xe_gf, td_gf, td64);
+      else substep_mixed(c, cd, cf, p, dt, s, xe_gf, td_gf, td_hp);
       if (!finite3(s.Tmu, s.xH2, s.xHp)) {
         s.status |= ST_NONFIN;
         s.t = dt;

@@ -69,6 +69,9 @@ def test_defaults_and_errors(tc):
     h = ctypes.c_void_p()
     assert tc.lib.tc_create(ctypes.byref(bad), ctypes.byref(h)) == tc.TC_EINVAL
     assert tc.lib.tc_peak_launch(99, 1, 32, 1, None, None) == tc.TC_EINVAL
+    assert tc.lib.tc_df64_eval(7, None, None, None, 1, None) == tc.TC_EINVAL
+    assert tc.lib.tc_df64_eval(0, None, None, None, 4, None) == tc.TC_EINVAL
+    assert tc.lib.tc_df64_eval(4, None, None, None, 0, None) == tc.TC_OK
 
 
 def _layout(src):
