@@ -38,6 +38,22 @@ int tc_peak_chains(void);
  * doubles; enqueued on `stream`.  Returns TC_OK, TC_EINVAL or TC_ECUDA.
  */
 int tc_df64_eval(int op, const double *a, const double *b, double *out, long long n, void *stream);
+
+/*
+ * tc_df64_source_check -- the heating/cooling and chemistry source terms of every cell of
+ * f at its stored state (T, x_H2, x_H+; C/O/e equilibrium and dust temperature solved),
+ * evaluated in df64 as the mixed kernels' polish does and in FP64, on the device.
+ * err (device, 5 * ncell doubles, SoA) receives per cell:
+ *   [0] |H_df - H| / (n G + n^2 |L|)       (H = n G - n^2 L, Eq. e:ODE1's source)
+ *   [1] |C_H2,df - C_H2| / (formation + destruction)
+ *   [2] |C_H+,df - C_H+| / (ionisation + recombination)
+ *   [3] relative error of the dust temperature,  [4] of x_e.
+ * p supplies the physics parameters (mode ignored); f's state is read only.  Enqueued
+ * on `stream`.  Returns TC_OK, TC_EINVAL (NULL or misaligned pointers) or TC_ECUDA.
+ */
+struct tc_params;
+struct tc_fields;
+int tc_df64_source_check(const struct tc_params *p, const struct tc_fields *f, double *err, void *stream);
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,7 @@
 #include "../../include/tc.h"
 #include "../../include/tc_onezone.h"
 #include "../../include/tc_pdr.h"
+#include "../../include/tc_peak.h"
 #include "tc_launch.h"
 #include "tc_mlp_mma.cuh"
 #include "tc_onezone.cuh"
@@ -234,6 +235,16 @@ static tcg::DevFields dev_fields(const tc_fields* f) {
   d.ncell = f->ncell;
   d.Zg_val = f->Zg_val; d.Zd_val = f->Zd_val;
   return d;
+}
+
+int tc_df64_source_check(const tc_params* p, const tc_fields* f, double* err, void* stream) {
+  if (!p || !err) return TC_EINVAL;
+  const int rc = check_fields(f);
+  if (rc != TC_OK || f->ncell == 0) return rc;
+  if (!aligned8(err)) return TC_EINVAL;
+  return tcg::launch_df64_source_check(dev_fields(f), dev_params(*p), err, (cudaStream_t)stream) == cudaSuccess
+             ? TC_OK
+             : TC_ECUDA;
 }
 
 static int kernel_mode(int mode) {

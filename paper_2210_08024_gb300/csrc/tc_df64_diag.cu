@@ -1,11 +1,12 @@
 // df64 (double-float) arithmetic on the device, built like the mixed step kernels (fast
-// FP32 intrinsics, flush-to-zero): element-wise evaluation for the accuracy tests and
-// throughput chains for the roofline of the mixed step (declared in include/tc_peak.h).
+// FP32 intrinsics, flush-to-zero): element-wise evaluation and the physics' source terms
+// in df64 against FP64, for the accuracy tests, and throughput chains for the roofline
+// of the mixed step (declared in include/tc_peak.h).
 #include <cuda_runtime.h>
 
 #include "../../include/tc.h"
 #include "../../include/tc_peak.h"
-#include "tc_df64.cuh"
+#include "tc_launch.h"
 
 namespace {
 using tcg::df64;
@@ -25,6 +26,34 @@ __global__ void k_df64_eval(int op, const double* __restrict__ a, const double* 
       default: r = tcg::m_log(x); break;
     }
     out[i] = double(r);
+  }
+}
+
+// Per cell at its stored state: the source terms in df64 against FP64 (errors as in
+// include/tc_peak.h, tc_df64_source_check), SoA in err[5 n].
+__global__ void __launch_bounds__(64) k_df64_source_check(tcg::DevFields f, tcg::DevParams p, double* err) {
+  using namespace tcg;
+  const long long n = f.ncell;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    CellC<double> c;
+    double T, x2, xp;
+    load_cell(f, i, p, c, T, x2, xp);
+    const CellC<df64> cd = cast_cell<df64>(c);
+    const double xH = 1.0 - 2.0 * x2 - xp;
+    const ChemT<double> b = chem_T(c, T, p.flags);
+    const CoolT<double> k = cool_T(c, b, p.flags);
+    const Equil<double> q = equilibrium(c, b, x2, xp, -1.0);
+    const Src<double> s = source(c, b, k, x2, xp, xH, q, -1.0, -1.0);
+    const ChemT<df64> bd = chem_T(cd, df64(T), p.flags);
+    const CoolT<df64> kd = cool_T(cd, bd, p.flags);
+    const Equil<df64> qd = equilibrium(cd, bd, df64(x2), df64(xp), df64(-1.0));
+    const Src<df64> sd = source(cd, bd, kd, df64(x2), df64(xp), df64(xH), qd, df64(-1.0), df64(-1.0));
+    const double nn = c.n;
+    err[i] = fabs(double(sd.H) - s.H) / (nn * fabs(s.G) + nn * nn * fabs(s.L));
+    err[n + i] = fabs(double(sd.CH2) - s.CH2) / fmax(s.form + s.dest, 1e-300);
+    err[2 * n + i] = fabs(double(sd.CHp) - s.CHp) / fmax(s.ion + s.rec, 1e-300);
+    err[3 * n + i] = fabs(double(sd.Td) - s.Td) / s.Td;
+    err[4 * n + i] = fabs(double(qd.xe) - q.xe) / q.xe;
   }
 }
 
@@ -59,8 +88,15 @@ extern "C" int tc_df64_eval(int op, const double* a, const double* b, double* ou
   return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ECUDA;
 }
 
-// The df64 kinds of tc_peak_launch (tc_peak.cu forwards them here).
 namespace tcg {
+cudaError_t launch_df64_source_check(const DevFields& f, const DevParams& p, double* err, cudaStream_t st) {
+  const long long want = (f.ncell + 63) / 64;
+  const int grid = (int)(want < 8192 ? want : 8192);
+  k_df64_source_check<<<grid, 64, 0, st>>>(f, p, err);
+  return cudaGetLastError();
+}
+
+// The df64 kinds of tc_peak_launch (tc_peak.cu forwards them here).
 int df64_peak_launch(int kind, int grid, int block, int iters, double* sink, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (kind == 9) k_df64_peak<9><<<grid, block, 0, st>>>(iters, sink);

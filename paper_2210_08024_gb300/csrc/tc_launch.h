@@ -27,4 +27,6 @@ cudaError_t launch_mode3(bool batch, const DevFields& f, const BoxTable* d_boxes
 cudaError_t launch_mode4(bool batch, const DevFields& f, const BoxTable* d_boxes, const DevParams& p, double dt,
                          unsigned long long* cursor, long long ntotal, int grid, int block, cudaStream_t st,
                          const MlpDev* mlp);
+// Device check of the df64 source terms (tc_df64_diag.cu; tc_df64_source_check).
+cudaError_t launch_df64_source_check(const DevFields& f, const DevParams& p, double* err, cudaStream_t st);
 }  // namespace tcg

@@ -142,6 +142,8 @@ def _load():
     L.tc_peak_chains.restype = ctypes.c_int
     L.tc_df64_eval.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
                                ctypes.c_void_p]
+    L.tc_df64_source_check.argtypes = [ctypes.POINTER(tc_params), ctypes.POINTER(tc_fields), ctypes.c_void_p,
+                                       ctypes.c_void_p]
     L.tc_step_host_static.argtypes = [ctypes.POINTER(tc_params), ctypes.POINTER(tc_fields), ctypes.c_double,
                                       ctypes.c_void_p]
     # seed network (include/tc_mlp.h)
@@ -332,6 +334,13 @@ def tc_peak_chains() -> int:
 
 
 DF64_OPS = {"add": 0, "mul": 1, "div": 2, "sqrt": 3, "exp": 4, "log": 5}
+
+
+def tc_df64_source_check(params, fields, err, stream=None) -> None:
+    """Source terms in df64 against FP64 at the stored state of every cell (include/tc_peak.h):
+    err is a contiguous CUDA float64 tensor of 5 * ncell values."""
+    _check(lib.tc_df64_source_check(ctypes.byref(params), ctypes.byref(fields), err.data_ptr(), _stream_ptr(stream)),
+           "tc_df64_source_check")
 
 
 def tc_df64_eval(op: str, a, b, out, stream=None) -> None:
