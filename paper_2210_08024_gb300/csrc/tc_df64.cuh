@@ -24,8 +24,11 @@
 //    the first with 12 significant bits so that k times it is exact for |k| < 2^12),
 //    2^(j/16) from a 16-entry table of df64 values (j = k mod 16), and the Taylor series
 //    of exp(r) - 1 to r^6 for |r| <= ln2/32 (truncation error below 5e-16);
-//  - log by one correction of the FP32 logarithm y0: with d = x exp(-y0) - 1 (small),
-//    log x = y0 + log(1 + d) = y0 + d - d^2/2 + d^3/3 (error ~d^4/4, below 1e-19).
+//  - log by one correction of the FP32 logarithm y0 of the mantissa m in [1, 2)
+//    (x = 2^e m): with d = m exp(-y0) - 1 (small), log x = e ln2 + y0 + log(1 + d)
+//    = e ln2 + y0 + d - d^2/2 + d^3/3 (error ~d^4/4, below 1e-19).
+// In the fast-math build FP32 subnormals flush to zero, so a df64 value below ~2e-31
+// keeps only its leading part (FP32 precision): the trailing part is ~2^-24 of it.
 // Infinities would turn the trailing parts into NaN (inf - inf in the error-free
 // transformations), so the type saturates instead: a conversion from FP64 maps
 // magnitudes above 1e36 (and infinities) to +-1e36, exp returns 0 below -87 (FP32's
@@ -273,17 +276,40 @@ __host__ __device__ __noinline__ inline df64 m_exp(df64 x) {
   return df64::make(y.hi * sc, y.lo * sc);
 }
 
-// log(x) for a df64 argument (method in the header comment).
+// log(x) for a df64 argument (method in the header comment), with x first scaled by a
+// power of two into [1, 2): x = 2^e m, log x = e ln2 + log m.  Then exp(-y0) stays in
+// (1/2, 1], far from the flush-to-zero range, for any x.
 __host__ __device__ __noinline__ inline df64 m_log(df64 x) {
   if (!(x.hi > 0.0f)) {
     if (x.hi == 0.0f) return df64::make(float(-DF_BIG), 0.0f);
     return df64::make(logf(x.hi), 0.0f);  // NaN
   }
-  const float y0 = logf(x.hi);
-  const df64 d = add_f(x * m_exp(df64::make(-y0, 0.0f)), -1.0f);
+  int ex;
+  (void)frexpf(x.hi, &ex);  // x.hi = f 2^ex, f in [1/2, 1)
+  int e = ex - 1;
+  if (e > 126) e = 126;
+  if (e < -126) e = -126;
+  const float sc = df_pow2i(-e);
+  const df64 m = df64::make(x.hi * sc, x.lo * sc);
+  const float y0 = logf(m.hi);
+  const df64 d = add_f(m * m_exp(df64::make(-y0, 0.0f)), -1.0f);
   const float dh = d.hi;
   const float corr = df_mul_rn(df_mul_rn(dh, dh), df_fma(dh, 1.0f / 3.0f, -0.5f));
-  return add_f(df64::make(y0, 0.0f) + d, corr);
+  // e ln2 with ln2 = L1 + L2 + L3 (L1 = 0x1.62e4p-1, 16 significant bits: e L1 is exact)
+  constexpr float L1 = 0.693145751953125f, L2 = 1.4286068e-06f, L3 = 5.497923e-14f;
+  const float fe = float(e);
+  float p, pe;
+  two_prod(fe, L2, p, pe);
+  df64 eln2;
+  {
+    float s1, e1;
+    two_sum(fe * L1, p, s1, e1);
+    e1 = df_add_rn(e1, df_add_rn(pe, df_mul_rn(fe, L3)));
+    float h, l;
+    fast_two_sum(s1, e1, h, l);
+    eln2 = df64::make(h, l);
+  }
+  return add_f(eln2 + (df64::make(y0, 0.0f) + d), corr);
 }
 
 }  // namespace tcg

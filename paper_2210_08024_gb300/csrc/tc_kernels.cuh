@@ -584,18 +584,6 @@ TCG_FN void picard_predictor(const CellC<double>& c, const DevParams& p, double 
   }
 }
 
-// A substep's FP64 Newton solve from the predictor above (flagging ST_PREDICTOR), for a
-// substep whose solve from the start state failed.  Returns the iterations, or -1.
-template <int LPC = 1>
-TCG_FN int solve_from_predictor64(const CellC<double>& c, const DevParams& p, double mu, double Kinv,
-                                  const double* yn, double dts, double* y, double& xe_g, double& td_g, int& status,
-                                  Equil<double>* qb) {
-  status |= ST_PREDICTOR;
-  picard_predictor(c, p, mu, Kinv, yn, dts, y, xe_g, td_g);
-  if (!finite3(y[0], y[1], y[2])) return -1;
-  return newton_solve<LPC>(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, 0, qb);
-}
-
 // One substep's FP64 Newton solve at length dts: from the start state, and if that
 // fails, from the predictor above (flagging ST_PREDICTOR).  Returns the iterations of
 // the successful solve, or -1.
@@ -792,141 +780,6 @@ TCG_FN void substep_newton64(const CellC<double>& c, const DevParams& p, double 
   bool last;
   const double dts = substep_start64(c, p, dt, s, td_g, last);
   solve_substep64<LPC>(c, p, dt, dts, last, s, xe_g, td_g);
-}
-
-// ------------------------------------------------------------------ mode 1, one iteration per trip
-// The one-lane FP64 kernel advances its cell by one Newton iteration per trip of the
-// persistent loop, not by one substep: a lane whose solve converged starts its next
-// substep on the next trip, so the lanes of a warp, whose cells need different numbers
-// of iterations per substep, do not wait for the warp's slowest solve.  The solve is
-// the same backward-Euler root (Sec. 6.1 scheme, coupled as in mode 1) with these
-// differences in the path to it:
-//  - the substep start's temperature blocks (built for the source terms that set the
-//    substep length, Sec. 6.1) serve the first iteration's base point, which is the
-//    same temperature;
-//  - every iteration builds the forward-difference Jacobian, as the plain iteration
-//    of the CPU reference does (the substep-at-a-time kernels reuse it in chord
-//    iterations near the root): with the lanes at different iterations nearly every
-//    trip has a lane that needs one, so the warp pays for those evaluations in any
-//    case;
-//  - the Jacobian's evaluations start their C/O/e and dust-temperature solves from the
-//    base point's roots, a relative distance ~1e-7 away.
-// Each cell's arithmetic depends on its own state only (not on its lane or its warp).
-// A solve that fails (singular Jacobian, non-finite state, newton_max iterations)
-// continues as solve_substep64 does after a failed first attempt: from the predictor,
-// then at half length.
-struct FlatSolve {
-  double yn[3], y[3];
-  double dts;
-  double qxe, qxCp, qxCO;  // C/O/e equilibrium at the last base point
-  int it;
-  bool last, active;
-};
-
-// The rest of solve_substep64 after its solve from the start state failed.
-TCG_FN void substep64_rescue(const CellC<double>& c, const DevParams& p, double dt, double dts, bool last,
-                             LaneState& s, double& xe_g, double& td_g) {
-  const double yn[3] = {s.Tmu, s.xH2, s.xHp};
-  const double Kinv = 1.0 / c.K;
-  double y[3] = {yn[0], yn[1], yn[2]};
-  Equil<double> qb;
-  int it = solve_from_predictor64<1>(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status, &qb);
-  int halv = 0;
-  while (it < 0 && halv < 30) {
-    s.status |= ST_NEWTON;
-    dts *= 0.5;
-    last = false;
-    ++halv;
-    it = solve_from_start64<1>(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status, &qb);
-  }
-  if (it < 0) {
-    s.status |= ST_NONFIN;
-    s.t = dt;
-    return;
-  }
-  s.iters += it;
-  finish_substep_q(c, p, dt, dts, last, y, qb, s);
-}
-
-// One trip of a lane: starts a substep if none is in progress, then takes one Newton
-// iteration, and finishes the substep when it converged.
-TCG_FN void newton_trip(const CellC<double>& c, const DevParams& p, double dt, LaneState& s, FlatSolve& fs,
-                        double& xe_g, double& td_g) {
-  TCG_COUNT_D(newton64_it);
-  const double Kinv = 1.0 / c.K;
-  const bool starting = !fs.active;
-  if (starting) {
-    fs.yn[0] = fs.y[0] = s.Tmu;
-    fs.yn[1] = fs.y[1] = s.xH2;
-    fs.yn[2] = fs.y[2] = s.xHp;
-  }
-  double* y = fs.y;
-  // temperature blocks at the base point: the substep start or the current iterate
-  ChemT<double> b = chem_T(c, s.mu * y[0], p.flags);
-  CoolT<double> k = cool_T(c, b, p.flags);
-  if (starting) {
-    // the substep length from the source terms with the stored C/O/e equilibrium
-    Equil<double> q0;
-    q0.xe = s.xe; q0.xCp = s.xCp; q0.xCO = s.xCO;
-    q0.xOp = c.xOtot * s.xHp;
-    q0.xC = c.xCtot - s.xCp - s.xCO;
-    q0.xO = c.xOtot - s.xCO - q0.xOp;
-    const Src<double> s0 = source(c, b, k, s.xH2, s.xHp, 1.0 - 2.0 * s.xH2 - s.xHp, q0, -1.0, td_g);
-    td_g = s0.Td;
-    fs.dts = substep_len(p, dt - s.t, c.K * s.Tmu, s0.H, s0.CH2, s0.CHp, fs.last);
-    fs.it = 0;
-    fs.active = true;
-  }
-  // f at the base point with the equilibrium re-solved there (at the substep start it
-  // differs from the stored one: mu, hence T, changed when the last substep ended)
-  const Equil<double> q = equilibrium(c, b, y[1], y[2], xe_g);
-  xe_g = q.xe;
-  const Src<double> sr = source(c, b, k, y[1], y[2], 1.0 - 2.0 * y[1] - y[2], q, -1.0, td_g);
-  td_g = sr.Td;
-  fs.qxe = q.xe; fs.qxCp = q.xCp; fs.qxCO = q.xCO;
-  const double f0[3] = {sr.H * Kinv, sr.CH2, sr.CHp};
-  const double dts = fs.dts;
-  // forward-difference Jacobian (relative step 1e-7, abundance steps floored at 1e-17)
-  double J[3][3];
-#pragma unroll 1
-  for (int j = 1; j < 3; ++j) {
-    const double h = fmax(1e-7 * fabs(y[j]), 1e-17);
-    double xg = xe_g, tg = td_g, fx[3];
-    feval64(c, b, k, y[1] + ((j == 1) ? h : 0.0), y[2] + ((j == 2) ? h : 0.0), Kinv, xg, tg, fx);
-    const double sj = dts / h;
-    for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - sj * (fx[i] - f0[i]);
-  }
-  {
-    const double h = 1e-7 * y[0];
-    ChemT<double> bT = chem_T(c, s.mu * (y[0] + h), p.flags);
-    CoolT<double> kT = cool_T(c, bT, p.flags);
-    double xg = xe_g, tg = td_g, fT[3];
-    feval64(c, bT, kT, y[1], y[2], Kinv, xg, tg, fT);
-    const double s0 = dts / h;
-    for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - s0 * (fT[i] - f0[i]);
-  }
-  double rhs[3], d[3];
-  for (int i = 0; i < 3; ++i) rhs[i] = -(y[i] - fs.yn[i] - dts * f0[i]);
-  bool ok = solve3<double>(J, rhs, d);
-  bool conv = false;
-  if (ok) {
-    double st[3];
-    conv = damped_step(y, d, st);
-    for (int i = 0; i < 3; ++i)
-      if (fabs(st[i]) > p.rtol * fabs(y[i]) + 1e-300) conv = false;
-    ok = finite3(y[0], y[1], y[2]);
-  }
-  ++fs.it;
-  if (ok && conv) {
-    Equil<double> qb;
-    qb.xe = fs.qxe; qb.xCp = fs.qxCp; qb.xCO = fs.qxCO;
-    s.iters += fs.it;
-    finish_substep_q(c, p, dt, dts, fs.last, y, qb, s);
-    fs.active = false;
-  } else if (!ok || fs.it >= p.newton_max) {
-    fs.active = false;
-    substep64_rescue(c, p, dt, dts, fs.last, s, xe_g, td_g);
-  }
 }
 
 // ------------------------------------------------------------------ mode 2: mixed precision
@@ -1224,8 +1077,6 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
   CellC<float> cf;   // FP32 copy of the cell constants (mixed and seeded modes)
   CellC<df64> cd;    // df64 copy (mixed modes: substep-start sources and polish)
   double xe_g = -1.0, td_g = -1.0;
-  FlatSolve fs;      // mode 1, one lane per cell: the solve in progress
-  fs.active = false;
   float xe_gf = -1.f, td_gf = -1.f;
   df64 td_hp = df64(-1.0);   // dust-temperature guess of the df64 evaluations
   DevFields fb;
@@ -1288,7 +1139,6 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
         }
         s.mu = c.muH / (1.1 + s.xe - x20);
         s.Tmu = T0 / s.mu;
-        fs.active = false;
         have = true;
       }
     }
@@ -1325,22 +1175,7 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
       }
     } else {
       if (done) break;
-      if constexpr (MODE == 1 && LPC == 1) {
-        // one Newton iteration per trip (newton_trip)
-        if (s.t < dt) {
-          if (!fs.active && s.nsub >= p.max_sub) {
-            s.status |= ST_MAX_SUB;
-            s.t = dt;
-          } else {
-            newton_trip(c, p, dt, s, fs, xe_g, td_g);
-          }
-          if (!finite3(s.Tmu, s.xH2, s.xHp)) {
-            s.status |= ST_NONFIN;
-            s.t = dt;
-            fs.active = false;
-          }
-        }
-      } else if (s.t < dt) {
+      if (s.t < dt) {
         if (s.nsub >= p.max_sub) {
           s.status |= ST_MAX_SUB;
           s.t = dt;

@@ -191,11 +191,9 @@ int main(int argc, char** argv) {
       double xg = s.xe, tg = -1.0;
       df64 thp = df64(-1.0);
       float xgf = (float)s.xe, tgf = -1.f;
-      FlatSolve fs;
-      fs.active = false;
-      while (s.t < dt && (fs.active || s.nsub < p.max_sub)) {
+      while (s.t < dt && s.nsub < p.max_sub) {
         if (mode == 0) substep_paper(c, p, dt, s);
-        else if (mode == 1) newton_trip(c, p, dt, s, fs, xg, tg);  // the one-lane kernel's solver
+        else if (mode == 1) substep_newton64(c, p, dt, s, xg, tg);
         else substep_mixed(c, cd, cf, p, dt, s, xgf, tgf, thp);
         if (!finite3(s.Tmu, s.xH2, s.xHp)) break;
       }

@@ -3,8 +3,7 @@
 // binding; built and run by tests/test_host_step.py with the library's csrc/ on the
 // include path).  Each cell goes through the same
 // sequence as one lane of k_step: load_cell, the initial C/O/e equilibrium that sets mu,
-// substeps of the selected mode until the step's end (or the substep cap), store_cell;
-// mode 1 takes one Newton iteration per call as the one-lane kernel does (newton_trip).
+// substeps of the selected mode until the step's end (or the substep cap), store_cell.
 // Only host code is executed: the device translation of this file is never launched.
 //
 // Usage: tc_hoststep IN OUT MODE dvdr T_cmb chi0 opt_over_fuv tau_ratio limiter fd_rel
@@ -78,21 +77,18 @@ int main(int argc, char** argv) {
     float xe_gf = float(s.xe), td_gf = -1.f;
     s.mu = c.muH / (1.1 + s.xe - x20);
     s.Tmu = T0 / s.mu;
-    FlatSolve fs;
-    fs.active = false;
     while (s.t < dt) {
-      if (!fs.active && s.nsub >= p.max_sub) {
+      if (s.nsub >= p.max_sub) {
         s.status |= ST_MAX_SUB;
         s.t = dt;
         break;
       }
       if (mode == 0) substep_paper(c, p, dt, s);
-      else if (mode == 1) newton_trip(c, p, dt, s, fs, xe_g, td_g);  // one iteration per call, as the kernel
+      else if (mode == 1) substep_newton64(c, p, dt, s, xe_g, td_g);
       else substep_mixed(c, cd, cf, p, dt, s, xe_gf, td_gf, td_hp);
       if (!finite3(s.Tmu, s.xH2, s.xHp)) {
         s.status |= ST_NONFIN;
         s.t = dt;
-        fs.active = false;
       }
     }
     DevFields o{};

@@ -7,11 +7,12 @@ largest errors of each operation and of the physics' terms against FP64 over see
 operands and over the cells of the slab and of random states; the GPU test runs the
 arithmetic as the fast-math kernels compile it.  Bounds: ~2^-44 per operation (the
 sloppy double-double forms and a two-digit division), exp relative error set by the
-argument's own representation (|x| 2^-48, 1.2e-13 at x = 80), log absolute error
-|log x| 2^-48; the rates and terms within 1e-11 relative; the cooling function L
-within 1e-9 (it can be a difference itself: the gas-dust term heats the gas where
-T_d > T, and cancels part of the line cooling); the net H = n G - n^2 L, what the
-polish's residual and the substep length use, within 1e-10 of its larger term."""
+argument's own representation (|x| 2^-48, 1.2e-13 at x = 80), log absolute error a
+few |log x| 2^-48 (the result's own representation and two additions); the rates and
+terms within 1e-11 relative; the cooling function L within 1e-9 (it can be a
+difference itself: the gas-dust term heats the gas where T_d > T, and cancels part of
+the line cooling); the net H = n G - n^2 L, what the polish's residual and the
+substep length use, within 1e-10 of its larger term on the host."""
 import json
 import os
 import shutil
@@ -26,7 +27,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2210_08024_gb300", "csrc")
 IN_KEYS = ("n", "chi_pe", "chi_lw", "f_h2", "f_c", "F_lyc", "xi", "Zg", "Zd", "T", "xH2", "xHp")
 
-OP_BOUNDS = {"add": 3e-14, "mul": 3e-14, "div": 6e-14, "sqrt": 3e-14, "exp": 2e-13, "log_abs": 4e-13, "conv": 4e-15}
+OP_BOUNDS = {"add": 3e-14, "mul": 3e-14, "div": 6e-14, "sqrt": 3e-14, "exp": 2e-13, "log_abs": 6e-13, "conv": 4e-15}
 TERM_BOUNDS = {"chem_T": 1e-11, "cool_T": 1e-11, "xe": 1e-11, "G": 1e-11, "L": 1e-9, "H": 1e-10, "form": 1e-11,
                "dest": 1e-11, "ion": 1e-11, "rec": 1e-11, "Td": 1e-10}
 
@@ -80,16 +81,16 @@ def tc():
 
 @pytest.mark.gpu
 def test_df64_device_matches_fp64(tc):
-    # Operands in [1e-12, 1e12]: the fast-math build flushes FP32 subnormals to zero, so
-    # a df64 value below ~2e-31 keeps only its leading part (FP32 precision); see the
-    # last check.  The physics' terms are tested at that level below.
+    # Operands in [1e-12, 1e12] and exp arguments above -55: the fast-math build flushes
+    # FP32 subnormals to zero, so a df64 value below ~2e-31 keeps only its leading part
+    # (FP32 precision; the last checks).  The physics' terms are tested below.
     import torch
     rng = np.random.default_rng(3)
     n = 1 << 18
     sgn = lambda: np.where(rng.random(n) < 0.5, -1.0, 1.0)
     a = sgn() * np.exp(rng.uniform(np.log(1e-12), np.log(1e12), n))
     b = sgn() * np.exp(rng.uniform(np.log(1e-12), np.log(1e12), n))
-    x = rng.uniform(-70.0, 80.0, n)
+    x = rng.uniform(-55.0, 80.0, n)
     y = np.exp(rng.uniform(np.log(1e-30), np.log(1e30), n))
     dev = lambda v: torch.from_numpy(np.ascontiguousarray(v)).cuda()
     out = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -113,6 +114,7 @@ def test_df64_device_matches_fp64(tc):
     # below the flush floor: FP32 precision, no worse
     t = np.full(n, 1e-16)
     assert rel(run("mul", t, t), t * t) <= 1.2e-7
+    assert rel(run("exp", np.full(n, -80.0)), np.exp(np.full(n, -80.0))) <= 1.2e-7
 
 
 @pytest.mark.gpu
@@ -130,6 +132,10 @@ def test_df64_source_terms_on_device(tc, workload):
     m = {k: float(np.max(e[i])) for i, k in enumerate(("H", "CH2", "CHp", "Td", "xe"))}
     print(workload, "device df64 source-term errors:", {k: "%.2e" % v for k, v in m.items()})
     assert np.all(np.isfinite(e))
-    bounds = {"H": TERM_BOUNDS["H"], "CH2": 1e-11, "CHp": 1e-11, "Td": TERM_BOUNDS["Td"], "xe": TERM_BOUNDS["xe"]}
+    # On the device the flush floor applies: the dust constants B = 2e-27 Z'_d c a
+    # (4.5e-31) and the gas-dust coefficient 3.2e-34 n Z'_d keep FP32 precision (~6e-8),
+    # which moves T_d by ~1e-8 relative, and cooling terms below ~1e-31 keep FP32
+    # precision too.  H stays within 1e-9 of its larger term, the polish's target.
+    bounds = {"H": 1e-9, "CH2": 1e-11, "CHp": 1e-11, "Td": 3e-8, "xe": TERM_BOUNDS["xe"]}
     for k, b in bounds.items():
         assert m[k] <= b, (k, m[k], b)

@@ -52,7 +52,11 @@ def test_static_entry_matches_host_entry_twice(tc):
         assert_fp64_parity(a, b, "static-vs-host n=%d" % n)
         for k in ("xe", "xCp", "xCO"):
             np.testing.assert_allclose(a[k], b[k], rtol=1e-9, atol=1e-14)
-        assert np.array_equal(a["nsub"], b["nsub"]) and np.array_equal(a["status"], b["status"])
+        # error bits equal; the informational ones (predictor restart and the like)
+        # belong to the solver's path, which differs between the one-lane kernel
+        # (one iteration per trip) and the four-lane one tc_step_host picks here
+        assert np.array_equal(a["nsub"], b["nsub"])
+        assert np.array_equal(a["status"] & tc.TC_ST_ERROR_MASK, b["status"] & tc.TC_ST_ERROR_MASK)
     st.close()
 
 
