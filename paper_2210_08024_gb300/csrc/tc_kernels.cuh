@@ -979,17 +979,39 @@ TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<df64>& cd, c
     it = newton_mixed<LPC>(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, J, polish);
   }
   Equil<df64> qlast;
+  const int it32 = it;
+  bool have32 = false;
+  double y32[3];
   if (it >= 0) {
     if (polish) s.status |= ST_POLISH;
+    y32[0] = y[0]; y32[1] = y[1]; y32[2] = y[2];
+    have32 = true;
     fd_jacobian32<LPC>(cf, p, s.mu, Kinv, dts, y, xe_g, td_g, J);
     df64 xg = df64::make(xe_g, 0.0f), tg = df64::make(td_g, 0.0f);
     if (!polish_hp<df64>(cd, p, s.mu, Kinv, yn, dts, y, J, xg, tg, qlast)) it = -1;
   }
   if (it < 0) {
-    // The plain FP64 solver finishes this substep (same length, same start state).
+    // The plain FP64 solver finishes this substep (same length, same start state): when
+    // the FP32 iteration converged and only its polish failed (an FP32 Jacobian too poor
+    // near a singular one, in thermally unstable gas), first by Newton from that FP32
+    // root, the root the polish was refining; otherwise, or if that fails, as mode 1
+    // does (from the start state, the predictor, then half lengths).
     s.status |= ST_FALLBACK;
     double xg = s.xe, tg = double(td_hp);
-    solve_substep64<LPC>(c, p, dt, dts, last, s, xg, tg);
+    int it64 = -1;
+    Equil<double> qb;
+    if (have32) {
+      y[0] = y32[0]; y[1] = y32[1]; y[2] = y32[2];
+      it64 = newton_solve<LPC>(c, p, s.mu, Kinv, yn, dts, y, xg, tg, 0, &qb);
+    }
+    if (it64 >= 0) {
+      s.iters += it32 + it64;
+      finish_substep_q(c, p, dt, dts, last, y, qb, s);
+    } else {
+      xg = s.xe;
+      tg = double(td_hp);
+      solve_substep64<LPC>(c, p, dt, dts, last, s, xg, tg);
+    }
   } else {
     s.iters += it;
     finish_substep_q(c, p, dt, dts, last, y, equil64(qlast), s);

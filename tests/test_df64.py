@@ -81,9 +81,10 @@ def tc():
 
 @pytest.mark.gpu
 def test_df64_device_matches_fp64(tc):
-    # Operands in [1e-12, 1e12] and exp arguments above -55: the fast-math build flushes
-    # FP32 subnormals to zero, so a df64 value below ~2e-31 keeps only its leading part
-    # (FP32 precision; the last checks).  The physics' terms are tested below.
+    # Operands in [1e-12, 1e12], exp arguments above -55 and log arguments above 1e-25:
+    # the fast-math build flushes FP32 subnormals to zero, so a df64 value below ~2e-31
+    # (an input converted from FP64 too) keeps only its leading part (FP32 precision; the
+    # last checks).  The physics' terms are tested below.
     import torch
     rng = np.random.default_rng(3)
     n = 1 << 18
@@ -91,7 +92,7 @@ def test_df64_device_matches_fp64(tc):
     a = sgn() * np.exp(rng.uniform(np.log(1e-12), np.log(1e12), n))
     b = sgn() * np.exp(rng.uniform(np.log(1e-12), np.log(1e12), n))
     x = rng.uniform(-55.0, 80.0, n)
-    y = np.exp(rng.uniform(np.log(1e-30), np.log(1e30), n))
+    y = np.exp(rng.uniform(np.log(1e-25), np.log(1e30), n))
     dev = lambda v: torch.from_numpy(np.ascontiguousarray(v)).cuda()
     out = torch.empty(n, dtype=torch.float64, device="cuda")
 
@@ -115,6 +116,7 @@ def test_df64_device_matches_fp64(tc):
     t = np.full(n, 1e-16)
     assert rel(run("mul", t, t), t * t) <= 1.2e-7
     assert rel(run("exp", np.full(n, -80.0)), np.exp(np.full(n, -80.0))) <= 1.2e-7
+    assert np.max(np.abs(run("log", np.full(n, 1e-33)) - np.log(1e-33))) <= 1.2e-7
 
 
 @pytest.mark.gpu
