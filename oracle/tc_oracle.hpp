@@ -729,11 +729,11 @@ template <class R> inline bool solve3(R J[3][3], R b[3], R d[3]) {
 // damping that keeps T_mu, x_H2, x_H+ and x_H positive (see below).  Converged
 // when every full (undamped) step satisfies |d_i| <= rtol |y_i| (READING: relative for
 // every component, so abundances as small as 1e-25 are still converged relatively).
-// Returns the iteration count, or -1 on failure.
+// Returns the iteration count, or -1 on failure (also after maxit iterations).
 template <class R> int newton_substep(const CellIn& c, const Params& p, const Pre<R>& P, R mu, const R* yn, R dts,
-                                      const R* seed, R* y) {
+                                      const R* seed, R* y, int maxit) {
   for (int i = 0; i < 3; ++i) y[i] = seed[i];
-  for (int it = 1; it <= p.newton_max; ++it) {
+  for (int it = 1; it <= maxit; ++it) {
     R f[3];
     f_coupled(c, p, P, mu, y, f);
     R J[3][3];
@@ -877,20 +877,24 @@ template <class R> void picard_predictor(const CellIn& c, const Params& p, const
   }
 }
 
-// One substep's Newton solve: from the start state; if that fails, from the predictor
-// above.  Returns the iterations of the successful solve, or -1; `pred` is set when
-// the predictor was used.
+// One substep's Newton solve: from the start state (at most newton_max iterations); if
+// that fails, from the predictor above, with RESCUE_ITER_FACTOR times as many
+// iterations (READING, same as for the predictor: in thermally unstable substeps the
+// damped iteration can crawl to the root, up to ~300 iterations measured, and the
+// alternative, halving the substep, changes the substep grid).  Returns the iterations
+// of the successful solve, or -1; `pred` is set when the predictor was used.
+constexpr int RESCUE_ITER_FACTOR = 8;
 template <class R> int solve_substep(const CellIn& c, const Params& p, const Pre<R>& P, R mu, const R* yn, R dts,
                                      R* y, bool& pred) {
   if (!(p.flags & F_PREDICTOR)) {
-    int it = newton_substep(c, p, P, mu, yn, dts, yn, y);
+    int it = newton_substep(c, p, P, mu, yn, dts, yn, y, p.newton_max);
     if (it >= 0) return it;
   }
   pred = true;
   R ys[3];
   picard_predictor(c, p, P, mu, yn, dts, ys);
   if (!finite_(ys[0]) || !finite_(ys[1]) || !finite_(ys[2])) return -1;
-  return newton_substep(c, p, P, mu, yn, dts, ys, y);
+  return newton_substep(c, p, P, mu, yn, dts, ys, y, RESCUE_ITER_FACTOR * p.newton_max);
 }
 
 template <class R> CellOut step_coupled(const CellIn& c, const Params& p, double T_in, double xH2_in, double xHp_in,

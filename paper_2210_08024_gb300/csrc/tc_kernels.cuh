@@ -458,7 +458,7 @@ template <int LPC = 1>
 TCG_FN int newton_solve(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
                         double dts, double* y, double& xe_g, double& td_g, int maxit = 0,
                         Equil<double>* qb = nullptr, int* spent = nullptr) {
-  const int nmax = (maxit > 0 && maxit < p.newton_max) ? maxit : p.newton_max;
+  const int nmax = (maxit > 0) ? maxit : p.newton_max;
   double Jk[3][3];
   bool reuse = false;
   double prev = 1.0;
@@ -584,9 +584,16 @@ TCG_FN void picard_predictor(const CellC<double>& c, const DevParams& p, double 
   }
 }
 
-// One substep's FP64 Newton solve at length dts: from the start state, and if that
-// fails, from the predictor above (flagging ST_PREDICTOR).  Returns the iterations of
-// the successful solve, or -1.
+// Iteration cap of the Newton solve from the predictor, in units of newton_max: in
+// thermally unstable substeps the damped iteration can take a few hundred iterations to
+// reach the root (measured up to ~300), and the alternative, halving the substep,
+// changes the substep grid and with it the result.
+constexpr int RESCUE_ITER_FACTOR = 8;
+
+// One substep's FP64 Newton solve at length dts: from the start state (newton_max
+// iterations), and if that fails, from the predictor above (flagging ST_PREDICTOR;
+// RESCUE_ITER_FACTOR newton_max iterations).  Returns the iterations of the successful
+// solve, or -1.
 template <int LPC = 1>
 TCG_FN int solve_from_start64(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
                               double dts, double* y, double& xe_g, double& td_g, int& status, Equil<double>* qb) {
@@ -596,7 +603,7 @@ TCG_FN int solve_from_start64(const CellC<double>& c, const DevParams& p, double
   status |= ST_PREDICTOR;
   picard_predictor(c, p, mu, Kinv, yn, dts, y, xe_g, td_g);
   if (!finite3(y[0], y[1], y[2])) return -1;
-  return newton_solve<LPC>(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, 0, qb);
+  return newton_solve<LPC>(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, RESCUE_ITER_FACTOR * p.newton_max, qb);
 }
 
 // A seeded Newton solve that has not converged after this many iterations is abandoned
@@ -731,7 +738,8 @@ TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double d
     double xg = xe_g, tg = td_g;
     int spent = 0;
     it = cf ? chord64_from_seed<LPC>(c, *cf, p, s.mu, Kinv, yn, dts, y, xg, tg, &qb, &spent)
-            : newton_solve<LPC>(c, p, s.mu, Kinv, yn, dts, y, xg, tg, SEED_MAXIT, &qb, &spent);
+            : newton_solve<LPC>(c, p, s.mu, Kinv, yn, dts, y, xg, tg, (SEED_MAXIT < p.newton_max) ? SEED_MAXIT : p.newton_max,
+                                &qb, &spent);
     if (it >= 0) {
       xe_g = xg; td_g = tg;
       s.status |= ST_SEEDED;
