@@ -43,13 +43,14 @@ UNIT = "cell-updates/s"
 FP64_NOMINAL_TFLOPS = 1.25
 
 STATE_KEYS = ("T", "xH2", "xHp")
-# DRAM bytes per cell of one k_step<1> launch, from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum on a 112^3 slab, profiles/k_step_fp64_slab128.md), scaled by cells:
-# 24.80 GB read + 22.99 GB written for 1,404,928 cells.  Almost all of it is the
-# per-thread stack (spilled registers and the structs the out-of-line physics calls pass)
-# of 8 resident blocks per SM, ~2 MB of local memory per SM, more than L1 and L2 hold;
-# at the kernel's speed that is ~230 GB/s, 3% of HBM.  The cells' own data are 152 B.
-TRAFFIC_BYTES_PER_CELL = 34016.5
+# DRAM bytes per cell of one k_step<1> launch on the 128^3 slab in the benchmark's shape
+# (128 threads, 8 blocks per SM), from ncu (dram__bytes_read.sum + dram__bytes_write.sum,
+# one pass, profiles/k_step_fp64_slab128.md): 39.55 GB read + 35.91 GB written for
+# 2,097,152 cells.  Almost all of it is the per-thread stack (the 64-register cap's
+# spills and the structs passed to the out-of-line physics): 3.4 KB per thread for 1024
+# resident threads per SM is ~530 MB, four times L2; at the kernel's speed ~260 GB/s,
+# 3% of HBM.  The cells' own data are 152 B.
+TRAFFIC_BYTES_PER_CELL = 35982.0
 
 
 def parse():
