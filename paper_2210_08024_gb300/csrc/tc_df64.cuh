@@ -20,10 +20,11 @@
 //    second FP32 quotient of the remainder (FP32 quotients good to 2 units in the last
 //    place, as the fast-math build's divide, give ~2^-44);
 //  - square root by one Newton correction of the FP32 root;
-//  - exp by Cody-Waite argument reduction x = k ln2/16 + r (ln2/16 in three FP32 pieces,
-//    the first with 12 significant bits so that k times it is exact for |k| < 2^12),
-//    2^(j/16) from a 16-entry table of df64 values (j = k mod 16), and the Taylor series
-//    of exp(r) - 1 to r^6 for |r| <= ln2/32 (truncation error below 5e-16);
+//  - exp by Cody-Waite argument reduction x = k ln2/64 + r (ln2/64 in three FP32 pieces,
+//    the first with 9 significant bits so that k times it is exact), 2^(j/64) from a
+//    64-entry table of df64 values (j = k mod 64), and the Taylor series of exp(r) - 1
+//    to r^5 for |r| <= ln2/128 (truncation error below 4e-17), of which only r + r^2/2
+//    needs df64;
 //  - log by one correction of the FP32 logarithm y0 of the mantissa m in [1, 2)
 //    (x = 2^e m): with d = m exp(-y0) - 1 (small), log x = e ln2 + y0 + log(1 + d)
 //    = e ln2 + y0 + d - d^2/2 + d^3/3 (error ~d^4/4, below 1e-19).
@@ -212,31 +213,48 @@ TCG_FN df64 m_sqrt(df64 a) {
   return df64::make(h, l);
 }
 
-// 2^(j/16), j = 0..15, split into leading and trailing FP32 parts at compile time.
+// 2^(j/64), j = 0..63 (values of the mathematical constants to 17 digits), split into
+// leading and trailing FP32 parts at compile time.
 #define TCG_DF_EXP2(v) {float(v), float((v) - double(float(v)))}
-#define TCG_DF_EXP2_TABLE                                                                                \
-  {TCG_DF_EXP2(1.0), TCG_DF_EXP2(1.0442737824274138), TCG_DF_EXP2(1.0905077326652577),               \
-   TCG_DF_EXP2(1.1387886347566916), TCG_DF_EXP2(1.189207115002721), TCG_DF_EXP2(1.241857812073484),   \
-   TCG_DF_EXP2(1.2968395546510096), TCG_DF_EXP2(1.3542555469368927), TCG_DF_EXP2(1.4142135623730951), \
-   TCG_DF_EXP2(1.4768261459394993), TCG_DF_EXP2(1.5422108254079407), TCG_DF_EXP2(1.6104903319492543), \
-   TCG_DF_EXP2(1.681792830507429), TCG_DF_EXP2(1.7562521603732995), TCG_DF_EXP2(1.8340080864093424),  \
-   TCG_DF_EXP2(1.9152065613971474)}
-static __device__ const float2 kDfExp2Dev[16] = TCG_DF_EXP2_TABLE;
-static const float2 kDfExp2Host[16] = TCG_DF_EXP2_TABLE;
+#define TCG_DF_EXP2_TABLE \
+  {TCG_DF_EXP2(1.0), TCG_DF_EXP2(1.0108892860517005), TCG_DF_EXP2(1.0218971486541166), \
+   TCG_DF_EXP2(1.0330248790212284), TCG_DF_EXP2(1.0442737824274138), TCG_DF_EXP2(1.0556451783605572), \
+   TCG_DF_EXP2(1.0671404006768237), TCG_DF_EXP2(1.0787607977571199), TCG_DF_EXP2(1.0905077326652577), \
+   TCG_DF_EXP2(1.1023825833078409), TCG_DF_EXP2(1.1143867425958924), TCG_DF_EXP2(1.1265216186082418), \
+   TCG_DF_EXP2(1.1387886347566916), TCG_DF_EXP2(1.1511892299529827), TCG_DF_EXP2(1.1637248587775775), \
+   TCG_DF_EXP2(1.1763969916502812), TCG_DF_EXP2(1.189207115002721), TCG_DF_EXP2(1.2021567314527031), \
+   TCG_DF_EXP2(1.215247359980469), TCG_DF_EXP2(1.22848053610687), TCG_DF_EXP2(1.241857812073484), \
+   TCG_DF_EXP2(1.2553807570246911), TCG_DF_EXP2(1.2690509571917332), TCG_DF_EXP2(1.2828700160787783), \
+   TCG_DF_EXP2(1.2968395546510096), TCG_DF_EXP2(1.3109612115247644), TCG_DF_EXP2(1.3252366431597413), \
+   TCG_DF_EXP2(1.3396675240533029), TCG_DF_EXP2(1.3542555469368927), TCG_DF_EXP2(1.3690024229745905), \
+   TCG_DF_EXP2(1.383909881963832), TCG_DF_EXP2(1.3989796725383112), TCG_DF_EXP2(1.4142135623730951), \
+   TCG_DF_EXP2(1.42961333839197), TCG_DF_EXP2(1.4451808069770467), TCG_DF_EXP2(1.460917794180647), \
+   TCG_DF_EXP2(1.4768261459394993), TCG_DF_EXP2(1.4929077282912648), TCG_DF_EXP2(1.5091644275934228), \
+   TCG_DF_EXP2(1.5255981507445384), TCG_DF_EXP2(1.5422108254079407), TCG_DF_EXP2(1.5590044002378369), \
+   TCG_DF_EXP2(1.5759808451078865), TCG_DF_EXP2(1.593142151342267), TCG_DF_EXP2(1.6104903319492543), \
+   TCG_DF_EXP2(1.6280274218573478), TCG_DF_EXP2(1.6457554781539649), TCG_DF_EXP2(1.6636765803267364), \
+   TCG_DF_EXP2(1.681792830507429), TCG_DF_EXP2(1.7001063537185235), TCG_DF_EXP2(1.7186192981224779), \
+   TCG_DF_EXP2(1.7373338352737062), TCG_DF_EXP2(1.7562521603732995), TCG_DF_EXP2(1.7753764925265212), \
+   TCG_DF_EXP2(1.7947090750031072), TCG_DF_EXP2(1.8142521755003989), TCG_DF_EXP2(1.8340080864093424), \
+   TCG_DF_EXP2(1.8539791250833855), TCG_DF_EXP2(1.8741676341103), TCG_DF_EXP2(1.8945759815869656), \
+   TCG_DF_EXP2(1.9152065613971474), TCG_DF_EXP2(1.9360617934922943), TCG_DF_EXP2(1.9571441241754002), \
+   TCG_DF_EXP2(1.9784560263879509)}
+static __device__ const float2 kDfExp2Dev[64] = TCG_DF_EXP2_TABLE;
+static const float2 kDfExp2Host[64] = TCG_DF_EXP2_TABLE;
 
 // exp(x) for a df64 argument (method in the header comment).
 __host__ __device__ __noinline__ inline df64 m_exp(df64 x) {
   if (x.hi < -87.0f) return df64::make(0.0f, 0.0f);
   if (x.hi > 80.0f) x = df64::make(80.0f, 0.0f);
   if (!(x.hi == x.hi)) return x;  // NaN
-  // ln2/16 = C1 + C2 + C3 (C1 = 0x1.62ep-5, 12 significant bits)
-  constexpr float C1 = 0.043319702148437500f;
-  constexpr float C2 = 1.9966365e-06f;
-  constexpr float C3 = 1.02912186e-13f;
-  constexpr float INV = 23.083120654223414f;  // 16 / ln 2
+  // ln2/64 = C1 + C2 + C3 (C1 = 0x1.63p-7, 9 significant bits: k C1 is exact for |k| < 2^15)
+  constexpr float C1 = 0.0108337402343750f;
+  constexpr float C2 = -3.3155382e-06f;
+  constexpr float C3 = 2.5728046e-14f;
+  constexpr float INV = 92.33248261689366f;  // 64 / ln 2
   const float kf = rintf(x.hi * INV);
   const int k = (int)kf;
-  // r = x - k ln2/16: x.hi - k C1 is exact (k C1 is exact, and within a factor 2 of x.hi)
+  // r = x - k ln2/64: x.hi - k C1 is exact (k C1 is exact, and within a factor 2 of x.hi)
   const float a = df_sub_rn(x.hi, df_mul_rn(kf, C1));
   df64 r;
   {
@@ -251,20 +269,25 @@ __host__ __device__ __noinline__ inline df64 m_exp(df64 x) {
     fast_two_sum(s2, e, h, l);
     r = df64::make(h, l);
   }
-  // exp(r) - 1 = r + r^2/2 + r^3/6 + r^4 (1/24 + r/120 + r^2/720); the last group is
-  // below 1e-8 and needs only FP32
-  const df64 r2 = r * r;
-  const df64 r3 = r2 * r;
-  const float rh = r.hi;
-  float q = df_fma(rh, 1.0f / 720.0f, 1.0f / 120.0f);
-  q = df_fma(rh, q, 1.0f / 24.0f);
-  q = df_mul_rn(df_mul_rn(r2.hi, r2.hi), q);
-  df64 em1 = r + df64::make(0.5f * r2.hi, 0.5f * r2.lo);
-  em1 = em1 + r3 * df64(1.0 / 6.0);
-  em1 = add_f(em1, q);
-  // exp(x) = 2^m 2^(j/16) (1 + em1) with k = 16 m + j
-  const int j = k & 15;
-  const int m = (k - j) / 16;
+  // exp(r) - 1 = r + r^2/2 + r^3 (1/6 + r/24 + r^2/120) for |r| <= ln2/128: r^2/2 in df64
+  // (its square exact from Dekker's product), the cubic group (below 3e-8) in FP32
+  df64 em1;
+  {
+    float p, pe;
+    two_prod(r.hi, r.hi, p, pe);
+    pe = df_fma(2.0f * r.hi, r.lo, pe);
+    float h, l;
+    fast_two_sum(0.5f * p, 0.5f * pe, h, l);
+    em1 = r + df64::make(h, l);
+    const float rh = r.hi;
+    float q = df_fma(rh, 1.0f / 120.0f, 1.0f / 24.0f);
+    q = df_fma(rh, q, 1.0f / 6.0f);
+    q = df_mul_rn(df_mul_rn(df_mul_rn(rh, rh), rh), q);
+    em1 = add_f(em1, q);
+  }
+  // exp(x) = 2^m 2^(j/64) (1 + em1) with k = 64 m + j
+  const int j = k & 63;
+  const int m = (k - j) / 64;
 #ifdef __CUDA_ARCH__
   const float2 t = __ldg(&kDfExp2Dev[j]);
 #else

@@ -1140,8 +1140,17 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
         s.nsub = 0;
         s.status = 0;
         s.iters = 0;
-        {
-          // initial C/O/e equilibrium (it sets mu and hence T_mu) in FP64 for every mode
+        if constexpr (MIXED) {
+          // initial C/O/e equilibrium (it sets mu and hence T_mu): in df64 in the mixed
+          // modes, whose FP64 physics then runs only in their rare fallbacks
+          cd = cast_cell<df64>(c);
+          ChemT<df64> b0 = chem_T(cd, df64(T0), p.flags);
+          Equil<df64> q0 = equilibrium(cd, b0, df64(x20), df64(xp0), df64(-1.0));
+          s.xe = double(q0.xe); s.xCp = double(q0.xCp); s.xCO = double(q0.xCO);
+          xe_g = s.xe;
+          td_g = -1.0;
+        } else {
+          // in FP64 in the FP64 modes
           ChemT<double> b0 = chem_T(c, T0, p.flags);
           Equil<double> q0 = equilibrium(c, b0, x20, xp0, -1.0);
           s.xe = q0.xe; s.xCp = q0.xCp; s.xCO = q0.xCO;
@@ -1153,10 +1162,7 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
           xe_gf = float(s.xe);
           td_gf = -1.f;
         }
-        if constexpr (MIXED) {
-          cd = cast_cell<df64>(c);
-          td_hp = df64(-1.0);
-        }
+        if constexpr (MIXED) td_hp = df64(-1.0);
         if constexpr (SEEDED) {
           const double chi_fuv = (1.8e-4 * fb.chi_pe[li] + 3.0e-5 * fb.chi_lw[li]) / 2.1e-4;
           const double Fl = fb.Flyc ? fb.Flyc[li] : 0.0;

@@ -183,9 +183,15 @@ int main(int argc, char** argv) {
       CellC<df64> cd = cast_cell<df64>(c);
       LaneState s;
       s.t = 0; s.xH2 = col(10)[i]; s.xHp = col(11)[i]; s.Td = -1; s.nsub = 0; s.status = 0; s.iters = 0;
-      ChemT<double> b0 = chem_T(c, col(9)[i], p.flags);
-      Equil<double> q0 = equilibrium(c, b0, s.xH2, s.xHp, -1.0);
-      s.xe = q0.xe; s.xCp = q0.xCp; s.xCO = q0.xCO;
+      if (mode == 2) {  // the mixed kernels solve the initial equilibrium in df64
+        ChemT<df64> b0 = chem_T(cd, df64(col(9)[i]), p.flags);
+        Equil<df64> q0 = equilibrium(cd, b0, df64(s.xH2), df64(s.xHp), df64(-1.0));
+        s.xe = double(q0.xe); s.xCp = double(q0.xCp); s.xCO = double(q0.xCO);
+      } else {
+        ChemT<double> b0 = chem_T(c, col(9)[i], p.flags);
+        Equil<double> q0 = equilibrium(c, b0, s.xH2, s.xHp, -1.0);
+        s.xe = q0.xe; s.xCp = q0.xCp; s.xCO = q0.xCO;
+      }
       s.mu = c.muH / (1.1 + s.xe - s.xH2);
       s.Tmu = col(9)[i] / s.mu;
       double xg = s.xe, tg = -1.0;

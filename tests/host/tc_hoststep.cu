@@ -67,12 +67,18 @@ int main(int argc, char** argv) {
     load_cell(f, i, p, c, T0, x20, xp0);
     LaneState s;
     s.t = 0.0; s.xH2 = x20; s.xHp = xp0; s.Td = -1.0; s.nsub = 0; s.status = 0; s.iters = 0;
-    ChemT<double> b0 = chem_T(c, T0, p.flags);
-    Equil<double> q0 = equilibrium(c, b0, x20, xp0, -1.0);
-    s.xe = q0.xe; s.xCp = q0.xCp; s.xCO = q0.xCO;
-    double xe_g = q0.xe, td_g = -1.0;
     CellC<float> cf = cast_cell<float>(c);
     CellC<df64> cd = cast_cell<df64>(c);
+    if (mode == 2) {  // the mixed kernels solve the initial equilibrium in df64
+      ChemT<df64> b0 = chem_T(cd, df64(T0), p.flags);
+      Equil<df64> q0 = equilibrium(cd, b0, df64(x20), df64(xp0), df64(-1.0));
+      s.xe = double(q0.xe); s.xCp = double(q0.xCp); s.xCO = double(q0.xCO);
+    } else {
+      ChemT<double> b0 = chem_T(c, T0, p.flags);
+      Equil<double> q0 = equilibrium(c, b0, x20, xp0, -1.0);
+      s.xe = q0.xe; s.xCp = q0.xCp; s.xCO = q0.xCO;
+    }
+    double xe_g = s.xe, td_g = -1.0;
     df64 td_hp = df64(-1.0);
     float xe_gf = float(s.xe), td_gf = -1.f;
     s.mu = c.muH / (1.1 + s.xe - x20);
