@@ -39,7 +39,9 @@ def _flags():
 # approximations.  Measured on the 128^3 slab (with an FP64 polish): mixed 250 -> 215 ms,
 # mixed + seed 295 -> 238 ms, with the same iteration counts and the same parity results.
 # tc_df64_diag.cu holds the device check of the df64 arithmetic, built the same way.
-FAST_FP32 = {"tc_k_mixed.cu", "tc_k_seeded3.cu", "tc_k_mixed_coop.cu", "tc_df64_diag.cu"}
+# tc_order.cu predicts each cell's cost class from FP32 source terms (its FP64 kernel,
+# k_rates, is untouched by the option).
+FAST_FP32 = {"tc_k_mixed.cu", "tc_k_seeded3.cu", "tc_k_mixed_coop.cu", "tc_df64_diag.cu", "tc_order.cu"}
 
 
 def _compile(src: str) -> tuple[str, str]:

@@ -634,7 +634,7 @@ TCG_FN void feval32(const CellC<float>& cf, const ChemT<float>& b, const CoolT<f
 // iterations earlier.  With LPC = 4 the four evaluations are split over the cell's lanes.
 template <int LPC = 1>
 TCG_FN void fd_jacobian32(const CellC<float>& cf, const DevParams& p, double mu, double Kinv, double dts,
-                          const double* y, float xe_g, float td_g, double J[3][3]) {
+                          const double* y, float xe_g, float td_g, float J[3][3]) {
   const double h0 = 1e-3 * y[0];
   const double h1 = fmax(1e-3 * fabs(y[1]), 1e-12), h2 = fmax(1e-3 * fabs(y[2]), 1e-12);
   double f0[3], f1[3], f2[3], fT[3];
@@ -668,11 +668,12 @@ TCG_FN void fd_jacobian32(const CellC<float>& cf, const DevParams& p, double mu,
     xg = xe_g; tg = td_g;
     feval32(cf, bT, kT, y[1], y[2], Kinv, xg, tg, fT);
   }
-  const double s0 = dts / h0, s1 = dts / h1, s2 = dts / h2;
+  // the differences of f in FP64 (nearby values), the columns in FP32
+  const float s0 = float(dts) / float(h0), s1 = float(dts) / float(h1), s2 = float(dts) / float(h2);
   for (int i = 0; i < 3; ++i) {
-    J[i][0] = ((i == 0) ? 1.0 : 0.0) - s0 * (fT[i] - f0[i]);
-    J[i][1] = ((i == 1) ? 1.0 : 0.0) - s1 * (f1[i] - f0[i]);
-    J[i][2] = ((i == 2) ? 1.0 : 0.0) - s2 * (f2[i] - f0[i]);
+    J[i][0] = ((i == 0) ? 1.f : 0.f) - s0 * float(fT[i] - f0[i]);
+    J[i][1] = ((i == 1) ? 1.f : 0.f) - s1 * float(f1[i] - f0[i]);
+    J[i][2] = ((i == 2) ? 1.f : 0.f) - s2 * float(f2[i] - f0[i]);
   }
 }
 
@@ -687,7 +688,7 @@ template <int LPC = 1>
 TCG_FN int chord64_from_seed(const CellC<double>& c, const CellC<float>& cf, const DevParams& p, double mu, double Kinv,
                              const double* yn, double dts, double* y, double& xe_g, double& td_g, Equil<double>* qb,
                              int* spent) {
-  double J[3][3];
+  float J[3][3];
   fd_jacobian32<LPC>(cf, p, mu, Kinv, dts, y, float(xe_g), float(td_g), J);
   double prev = -1.0;
   for (int it = 1; it <= SEED_MAXIT + 2; ++it) {
@@ -700,7 +701,7 @@ TCG_FN int chord64_from_seed(const CellC<double>& c, const CellC<float>& cf, con
     double Jw[3][3], rhs[3], d[3];
     for (int i = 0; i < 3; ++i) {
       rhs[i] = -(y[i] - yn[i] - dts * f0[i]);
-      for (int jj = 0; jj < 3; ++jj) Jw[i][jj] = J[i][jj];
+      for (int jj = 0; jj < 3; ++jj) Jw[i][jj] = double(J[i][jj]);
     }
     if (!solve3<double>(Jw, rhs, d)) return -1;
     double st[3];
@@ -802,11 +803,11 @@ TCG_FN void substep_newton64(const CellC<double>& c, const DevParams& p, double 
 // of large terms; or -1 if neither happened.  J holds the last Jacobian on return.
 template <int LPC = 1>
 TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, double Kinv, const double* yn,
-                        double dts, double* y, float& xe_g, float& td_g, double J[3][3], bool& polish,
+                        double dts, double* y, float& xe_g, float& td_g, float J[3][3], bool& polish,
                         int maxit = 0, int* spent = nullptr) {
   bool haveJ = false;
   int rebuilt = 0;
-  double prev = 1e300;
+  float prev = 3e38f;
   polish = false;
   const int nmax = (maxit > 0 && maxit < p.newton_max) ? maxit : p.newton_max;
   for (int it = 1; it <= nmax; ++it) {
@@ -827,14 +828,14 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
         CoolT<float> k = cool_T(cf, b, p.flags);
         feval32(cf, b, k, y[1] + ((q == 1) ? h1 : 0.0), y[2] + ((q == 2) ? h2 : 0.0), Kinv, xg, tg, fq);
       }
-      const double s0 = dts / h0, s1 = dts / h1, s2 = dts / h2;
+      const float s0 = float(dts) / float(h0), s1 = float(dts) / float(h1), s2 = float(dts) / float(h2);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         f0[i] = from_lane<LPC>(fq[i], 0);
         const double f1 = from_lane<LPC>(fq[i], 1), f2 = from_lane<LPC>(fq[i], 2), fT = from_lane<LPC>(fq[i], 3);
-        J[i][1] = ((i == 1) ? 1.0 : 0.0) - s1 * (f1 - f0[i]);
-        J[i][2] = ((i == 2) ? 1.0 : 0.0) - s2 * (f2 - f0[i]);
-        J[i][0] = ((i == 0) ? 1.0 : 0.0) - s0 * (fT - f0[i]);
+        J[i][1] = ((i == 1) ? 1.f : 0.f) - s1 * float(f1 - f0[i]);
+        J[i][2] = ((i == 2) ? 1.f : 0.f) - s2 * float(f2 - f0[i]);
+        J[i][0] = ((i == 0) ? 1.f : 0.f) - s0 * float(fT - f0[i]);
       }
       xe_g = from_lane<LPC>(xg, 0);
       td_g = from_lane<LPC>(tg, 0);
@@ -853,8 +854,8 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
         float xg = xe_g, tg = td_g;
         double fx[3];
         feval32(cf, b, k, y1, y2, Kinv, xg, tg, fx);
-        const double sj = dts / h;
-        for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - sj * (fx[i] - f0[i]);
+        const float sj = float(dts) / float(h);
+        for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.f : 0.f) - sj * float(fx[i] - f0[i]);
       }
       const double h = 1e-3 * y[0];
       ChemT<float> bT = chem_T(cf, float(mu * (y[0] + h)), p.flags);
@@ -862,8 +863,8 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
       float xg = xe_g, tg = td_g;
       double fT[3];
       feval32(cf, bT, kT, y[1], y[2], Kinv, xg, tg, fT);
-      const double s0 = dts / h;
-      for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - s0 * (fT[i] - f0[i]);
+      const float s0 = float(dts) / float(h);
+      for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.f : 0.f) - s0 * float(fT[i] - f0[i]);
       haveJ = true;
     }
     }
@@ -871,20 +872,22 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
     float Jw[3][3], rhs[3], d32[3];
     for (int i = 0; i < 3; ++i) {
       rhs[i] = float(-(y[i] - yn[i] - dts * f0[i]));
-      for (int j = 0; j < 3; ++j) Jw[i][j] = float(J[i][j]);
+      for (int j = 0; j < 3; ++j) Jw[i][j] = J[i][j];
     }
     if (!solve3<float>(Jw, rhs, d32)) return -1;
     const double d[3] = {double(d32[0]), double(d32[1]), double(d32[2])};
     double st[3];
     const bool full = damped_step(y, d, st);
-    double nrm = 0.0;
+    // the convergence measure in FP32 (a ratio of step to tolerance)
+    float nrm = 0.f;
+    const float rtm = float(p.rtol_mixed);
     for (int i = 0; i < 3; ++i)
-      nrm = fmax(nrm, fabs(st[i]) / (p.rtol_mixed * fabs(y[i]) + ((i == 0) ? 1e-300 : 1e-12)));
+      nrm = fmaxf(nrm, fabsf(float(st[i])) / (rtm * fabsf(float(y[i])) + ((i == 0) ? 1e-30f : 1e-12f)));
     if (!finite3(y[0], y[1], y[2])) return -1;
     if (full) {
-      if (nrm <= 1.0) return it;
-      if (it >= 2 && nrm > 0.3 * prev) {
-        if (nrm > 0.7 * prev && nrm * p.rtol_mixed <= 1e-4) {
+      if (nrm <= 1.f) return it;
+      if (it >= 2 && nrm > 0.3f * prev) {
+        if (nrm > 0.7f * prev && nrm * rtm <= 1e-4f) {
           polish = true;
           return it;
         }
@@ -921,7 +924,7 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
 // `qlast` receives the C/O/e equilibrium of the last evaluation.
 template <class F>
 TCG_FN bool polish_hp(const CellC<F>& c, const DevParams& p, double mu, double Kinv, const double* yn, double dts,
-                      double* y, const double J[3][3], F& xe_g, F& td_g, Equil<F>& qlast) {
+                      double* y, const float J[3][3], F& xe_g, F& td_g, Equil<F>& qlast) {
   double prev = -1.0;
   for (int it = 0; it < 5; ++it) {
     TCG_COUNT_D(polish_it);
@@ -934,7 +937,7 @@ TCG_FN bool polish_hp(const CellC<F>& c, const DevParams& p, double mu, double K
     float Jw[3][3], rhs[3], d32[3];
     for (int i = 0; i < 3; ++i) {
       rhs[i] = float(-(y[i] - yn[i] - dts * f0[i]));
-      for (int j = 0; j < 3; ++j) Jw[i][j] = float(J[i][j]);
+      for (int j = 0; j < 3; ++j) Jw[i][j] = J[i][j];
     }
     if (!solve3<float>(Jw, rhs, d32)) return false;
     const double d[3] = {double(d32[0]), double(d32[1]), double(d32[2])};
@@ -974,7 +977,7 @@ TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<df64>& cd, c
   const double Kinv = 1.0 / c.K;
   double y[3] = {yn[0], yn[1], yn[2]};
   if (seed) { y[0] = seed[0]; y[1] = seed[1]; y[2] = seed[2]; }
-  double J[3][3];
+  float J[3][3];
   bool polish = false;
   int spent = 0;
   int it = newton_mixed<LPC>(cf, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, J, polish, seed ? SEED_MAXIT : 0, &spent);

@@ -10,7 +10,7 @@
 // 511 to 331 ms and mixed from 352 to 177 ms.  Results do not depend on the order.
 //
 //   k_order_key      one thread per cell: initial C/O/e equilibrium, start-state sources
-//                    in FP64 (as the step computes them), cost class, block histogram
+//                    (in FP32: they only pick a class), cost class, block histogram
 //   k_order_scan     exclusive scan of the ORDER_BUCKETS counts (one warp)
 //   k_order_scatter  one thread per cell: position = class offset + rank (warp-aggregated
 //                    atomics); cells of one class keep no particular order
@@ -58,20 +58,25 @@ __global__ void __launch_bounds__(128) k_order_key(DevFields f1, const BoxTable*
       atomicAdd(&sh[kh], 1u);
       continue;
     }
+    // The prediction only picks a quarter-octave class, so it is evaluated in FP32 (fast
+    // intrinsics, this translation unit): the initial C/O/e equilibrium and the start
+    // state's sources cost ~2000 FP64 FMA slots per cell, 8 ms on the 128^3 slab.
     CellC<double> c;
     double T0, x20, xp0;
     load_cell(fb, li, p, c, T0, x20, xp0);
+    const CellC<float> cf = cast_cell<float>(c);
     LaneState s;
     s.t = 0.0;
     s.xH2 = x20;
     s.xHp = xp0;
-    ChemT<double> b0 = chem_T(c, T0, p.flags);
-    Equil<double> q0 = equilibrium(c, b0, x20, xp0, -1.0);
-    s.xe = q0.xe; s.xCp = q0.xCp; s.xCO = q0.xCO;
+    ChemT<float> b0 = chem_T(cf, float(T0), p.flags);
+    Equil<float> q0 = equilibrium(cf, b0, float(x20), float(xp0), -1.f);
+    s.xe = double(q0.xe); s.xCp = double(q0.xCp); s.xCO = double(q0.xCO);
     s.mu = c.muH / (1.1 + s.xe - x20);
     s.Tmu = T0 / s.mu;
-    double td = -1.0, H0, CH2, CHp;
-    start_sources<double>(c, p, s, td, H0, CH2, CHp);
+    float td = -1.f;
+    double H0, CH2, CHp;
+    start_sources<float>(cf, p, s, td, H0, CH2, CHp);
     // r = dt / dts_1 without the cap at dt: the predicted substep count above 1, and
     // below 1 how far the state moves within its single substep (more Newton iterations
     // the closer r is to 1: 3.0 at r ~ 2^-10, 4.1 at r ~ 2^-1 on the slab).  Classes are
