@@ -405,22 +405,22 @@ TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, do
       for (int j = 0; j < 3; ++j) Jk[i][j] = J[i][j];
   } else {
     TCG_COUNT_D(newton64_it);
-    // evaluation order: x_H2 column, x_H+ column, base point (all at the base T), then
-    // the T_mu column, so the temperature blocks are built twice per iteration.
+    // evaluation order: base point, x_H2 column, x_H+ column (all at the base T), then
+    // the T_mu column, so the temperature blocks are built twice per iteration.  The
+    // columns start their C/O/e and dust-temperature solves from the base point's roots,
+    // ~1e-7 away (1.8 instead of 1.9 C/O/e and 1.5 instead of 2.0 dust iterations per
+    // evaluation on the slab).
     ChemT<double> b = chem_T(c, mu * y[0], p.flags);
     CoolT<double> k = cool_T(c, b, p.flags);
-    double fx[2][3];
+    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, qb);
 #pragma unroll 1
     for (int j = 1; j < 3; ++j) {
-      double h = fmax(1e-7 * fabs(y[j]), 1e-17);
-      double y1 = y[1] + ((j == 1) ? h : 0.0), y2 = y[2] + ((j == 2) ? h : 0.0);
-      double xg = xe_g, tg = td_g;
-      feval64(c, b, k, y1, y2, Kinv, xg, tg, fx[j - 1]);
-    }
-    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, qb);
-    for (int j = 1; j < 3; ++j) {
-      const double sj = dts / fmax(1e-7 * fabs(y[j]), 1e-17);
-      for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - sj * (fx[j - 1][i] - f0[i]);
+      const double h = fmax(1e-7 * fabs(y[j]), 1e-17);
+      const double y1 = y[1] + ((j == 1) ? h : 0.0), y2 = y[2] + ((j == 2) ? h : 0.0);
+      double xg = xe_g, tg = td_g, fx[3];
+      feval64(c, b, k, y1, y2, Kinv, xg, tg, fx);
+      const double sj = dts / h;
+      for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - sj * (fx[i] - f0[i]);
     }
     {
       double h = 1e-7 * y[0];
