@@ -360,7 +360,8 @@ constexpr double JAC_REUSE = 1e-3;
 template <int LPC = 1>
 TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
                        double dts, double* y, double& xe_g, double& td_g, double (*Jk)[3], bool reuse,
-                       double& rel, bool& full, Equil<double>* qb) {
+                       double& rel, bool& full, Equil<double>* qb,
+                       const ChemT<double>* b0 = nullptr, const CoolT<double>* k0 = nullptr) {
   double f0[3], J[3][3];
   if (reuse) {
     TCG_COUNT_D(chord64_it);
@@ -410,8 +411,17 @@ TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, do
     // columns start their C/O/e and dust-temperature solves from the base point's roots,
     // ~1e-7 away (1.8 instead of 1.9 C/O/e and 1.5 instead of 2.0 dust iterations per
     // evaluation on the slab).
-    ChemT<double> b = chem_T(c, mu * y[0], p.flags);
-    CoolT<double> k = cool_T(c, b, p.flags);
+    // the temperature blocks at the base point: given by the caller at a substep's first
+    // iteration (the substep start's, the same temperature), else built here
+    ChemT<double> b;
+    CoolT<double> k;
+    if (b0) {
+      b = *b0;
+      k = *k0;
+    } else {
+      b = chem_T(c, mu * y[0], p.flags);
+      k = cool_T(c, b, p.flags);
+    }
     feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, qb);
 #pragma unroll 1
     for (int j = 1; j < 3; ++j) {
@@ -457,7 +467,8 @@ TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, do
 template <int LPC = 1>
 TCG_FN int newton_solve(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
                         double dts, double* y, double& xe_g, double& td_g, int maxit = 0,
-                        Equil<double>* qb = nullptr, int* spent = nullptr) {
+                        Equil<double>* qb = nullptr, int* spent = nullptr,
+                        const ChemT<double>* b0 = nullptr, const CoolT<double>* k0 = nullptr) {
   const int nmax = (maxit > 0) ? maxit : p.newton_max;
   double Jk[3][3];
   bool reuse = false;
@@ -465,7 +476,8 @@ TCG_FN int newton_solve(const CellC<double>& c, const DevParams& p, double mu, d
   for (int it = 1; it <= nmax; ++it) {
     double rel;
     bool full;
-    const int r = newton_iter<LPC>(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, Jk, reuse, rel, full, qb);
+    const int r = newton_iter<LPC>(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, Jk, reuse, rel, full, qb,
+                                   (it == 1) ? b0 : nullptr, (it == 1) ? k0 : nullptr);
     if (spent) *spent = it;
     if (r < 0) return -1;
     if (r > 0) return it;
@@ -479,10 +491,11 @@ TCG_FN int newton_solve(const CellC<double>& c, const DevParams& p, double mu, d
 // with the dust temperature solved; gives the substep length of Sec. 6.1.
 template <class F>
 TCG_FN void start_sources(const CellC<F>& cf, const DevParams& p, const LaneState& s, F& td_g, double& H0,
-                          double& CH2, double& CHp) {
+                          double& CH2, double& CHp, ChemT<F>* bo = nullptr, CoolT<F>* ko = nullptr) {
   const double T = s.mu * s.Tmu;
   ChemT<F> b = chem_T(cf, F(T), p.flags);
   CoolT<F> k = cool_T(cf, b, p.flags);
+  if (bo) { *bo = b; *ko = k; }
   Equil<F> q;
   q.xe = F(s.xe); q.xCp = F(s.xCp); q.xCO = F(s.xCO);
   q.xOp = cf.xOtot * F(s.xHp);
@@ -596,9 +609,10 @@ constexpr int RESCUE_ITER_FACTOR = 8;
 // solve, or -1.
 template <int LPC = 1>
 TCG_FN int solve_from_start64(const CellC<double>& c, const DevParams& p, double mu, double Kinv, const double* yn,
-                              double dts, double* y, double& xe_g, double& td_g, int& status, Equil<double>* qb) {
+                              double dts, double* y, double& xe_g, double& td_g, int& status, Equil<double>* qb,
+                              const ChemT<double>* b0 = nullptr, const CoolT<double>* k0 = nullptr) {
   y[0] = yn[0]; y[1] = yn[1]; y[2] = yn[2];
-  int it = newton_solve<LPC>(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, 0, qb);
+  int it = newton_solve<LPC>(c, p, mu, Kinv, yn, dts, y, xe_g, td_g, 0, qb, nullptr, b0, k0);
   if (it >= 0) return it;
   status |= ST_PREDICTOR;
   picard_predictor(c, p, mu, Kinv, yn, dts, y, xe_g, td_g);
@@ -728,7 +742,8 @@ TCG_FN int chord64_from_seed(const CellC<double>& c, const CellC<float>& cf, con
 template <int LPC = 1>
 TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double dt, double dts, bool last,
                             LaneState& s, double& xe_g, double& td_g, const double* seed = nullptr,
-                            const CellC<float>* cf = nullptr) {
+                            const CellC<float>* cf = nullptr,
+                            const ChemT<double>* b0 = nullptr, const CoolT<double>* k0 = nullptr) {
   const double yn[3] = {s.Tmu, s.xH2, s.xHp};
   const double Kinv = 1.0 / c.K;
   double y[3] = {yn[0], yn[1], yn[2]};
@@ -749,14 +764,15 @@ TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double d
       s.status |= ST_SEED_FAIL;
     }
   }
-  if (it < 0) it = solve_from_start64<LPC>(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status, &qb);
+  // b0, k0: the temperature blocks at the start state, if the caller has them
+  if (it < 0) it = solve_from_start64<LPC>(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status, &qb, b0, k0);
   int halv = 0;
   while (it < 0 && halv < 30) {
     s.status |= ST_NEWTON;
     dts *= 0.5;
     last = false;
     ++halv;
-    it = solve_from_start64<LPC>(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status, &qb);
+    it = solve_from_start64<LPC>(c, p, s.mu, Kinv, yn, dts, y, xe_g, td_g, s.status, &qb, b0, k0);
   }
   if (it < 0) {
     s.status |= ST_NONFIN;
@@ -772,23 +788,33 @@ TCG_FN void solve_substep64(const CellC<double>& c, const DevParams& p, double d
 // factor.  `src`, when given, receives those terms (H, C_H2, C_H+).
 template <class F>
 TCG_FN double substep_start_t(const CellC<F>& cc, double K, const DevParams& p, double dt, const LaneState& s,
-                              F& td_g, bool& last, double* src = nullptr) {
+                              F& td_g, bool& last, double* src = nullptr, ChemT<F>* bo = nullptr,
+                              CoolT<F>* ko = nullptr) {
   double H0, CH2, CHp;
-  start_sources<F>(cc, p, s, td_g, H0, CH2, CHp);
+  start_sources<F>(cc, p, s, td_g, H0, CH2, CHp, bo, ko);
   if (src) { src[0] = H0; src[1] = CH2; src[2] = CHp; }
   return substep_len(p, dt - s.t, K * s.Tmu, H0, CH2, CHp, last);
 }
 TCG_FN double substep_start64(const CellC<double>& c, const DevParams& p, double dt, const LaneState& s,
-                              double& td_g, bool& last, double* src = nullptr) {
-  return substep_start_t<double>(c, c.K, p, dt, s, td_g, last, src);
+                              double& td_g, bool& last, double* src = nullptr, ChemT<double>* bo = nullptr,
+                              CoolT<double>* ko = nullptr) {
+  return substep_start_t<double>(c, c.K, p, dt, s, td_g, last, src, bo, ko);
 }
 
 template <int LPC = 1>
 TCG_FN void substep_newton64(const CellC<double>& c, const DevParams& p, double dt, LaneState& s, double& xe_g,
                              double& td_g) {
   bool last;
-  const double dts = substep_start64(c, p, dt, s, td_g, last);
-  solve_substep64<LPC>(c, p, dt, dts, last, s, xe_g, td_g);
+  if constexpr (LPC == 1) {
+    // the start's temperature blocks serve the first Newton iteration (same T)
+    ChemT<double> b0;
+    CoolT<double> k0;
+    const double dts = substep_start64(c, p, dt, s, td_g, last, nullptr, &b0, &k0);
+    solve_substep64<LPC>(c, p, dt, dts, last, s, xe_g, td_g, nullptr, nullptr, &b0, &k0);
+  } else {
+    const double dts = substep_start64(c, p, dt, s, td_g, last);
+    solve_substep64<LPC>(c, p, dt, dts, last, s, xe_g, td_g);
+  }
 }
 
 // ------------------------------------------------------------------ mode 2: mixed precision
