@@ -175,7 +175,7 @@ TCG_FN df64 add_f(df64 a, float b) {
 
 // The quotients are FP32 divisions, not products with a reciprocal: the reciprocal of
 // a subnormal divisor overflows, and 0 times it would give NaN where the quotient is 0.
-TCG_FN df64 operator/(df64 a, df64 b) {
+__host__ __device__ __noinline__ inline df64 operator/(df64 a, df64 b) {
   const float q1 = a.hi / b.hi;
   const df64 r = a - mul_f(b, q1);  // the remainder, ~2^-22 of a
   const float q2 = r.hi / b.hi;
@@ -200,7 +200,7 @@ TCG_FN df64 m_abs(df64 a) { return (a.hi < 0.0f) ? -a : a; }
 TCG_FN df64 m_max(df64 a, df64 b) { return (a < b) ? b : a; }
 TCG_FN df64 m_min(df64 a, df64 b) { return (b < a) ? b : a; }
 
-TCG_FN df64 m_sqrt(df64 a) {
+__host__ __device__ __noinline__ inline df64 m_sqrt(df64 a) {
   if (!(a.hi > 0.0f)) return df64::make(sqrtf(a.hi), 0.0f);  // 0, or NaN below 0
   const float s = sqrtf(a.hi);
   float p, e;
