@@ -232,8 +232,8 @@ TCG_FN void substep_paper(const CellC<double>& c, const DevParams& p, double dt,
 // receives the C/O/e equilibrium of the evaluation.
 template <class F>
 TCG_FN void feval_t(const CellC<F>& c, const ChemT<F>& b, const CoolT<F>& k, double y1, double y2, double Kinv,
-                    F& xe_guess, F& td_guess, double* f, Equil<F>* qout = nullptr) {
-  Equil<F> q = equilibrium(c, b, F(y1), F(y2), xe_guess);
+                    F& xe_guess, F& td_guess, double* f, Equil<F>* qout = nullptr, int eq_newton_max = 100) {
+  Equil<F> q = equilibrium(c, b, F(y1), F(y2), xe_guess, eq_newton_max);
   if (qout) *qout = q;
   Src<F> s = source(c, b, k, F(y1), F(y2), F(1.0 - 2.0 * y1 - y2), q, F(-1.0), td_guess);
   xe_guess = q.xe;
@@ -244,8 +244,8 @@ TCG_FN void feval_t(const CellC<F>& c, const ChemT<F>& b, const CoolT<F>& k, dou
 }
 TCG_FN void feval64(const CellC<double>& c, const ChemT<double>& b, const CoolT<double>& k, double y1,
                     double y2, double Kinv, double& xe_guess, double& td_guess, double* f,
-                    Equil<double>* qout = nullptr) {
-  feval_t<double>(c, b, k, y1, y2, Kinv, xe_guess, td_guess, f, qout);
+                    Equil<double>* qout = nullptr, int eq_newton_max = 100) {
+  feval_t<double>(c, b, k, y1, y2, Kinv, xe_guess, td_guess, f, qout, eq_newton_max);
 }
 
 // The FP64 fields of a C/O/e equilibrium solved in precision F.
@@ -409,10 +409,10 @@ TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, do
     // evaluation order: base point, x_H2 column, x_H+ column (all at the base T), then
     // the T_mu column, so the temperature blocks are built twice per iteration.  The
     // columns start their C/O/e and dust-temperature solves from the base point's roots,
-    // ~1e-7 away (1.8 instead of 1.9 C/O/e and 1.5 instead of 2.0 dust iterations per
-    // evaluation on the slab).
-    // the temperature blocks at the base point: given by the caller at a substep's first
-    // iteration (the substep start's, the same temperature), else built here
+    // ~1e-7 away, and take one Newton step of the C/O/e balance (converged to ~1e-14
+    // from there; the loop would take a second to confirm it).  The temperature blocks
+    // at the base point are given by the caller at a substep's first iteration (the
+    // substep start's, the same temperature), else built here.
     ChemT<double> b;
     CoolT<double> k;
     if (b0) {
@@ -428,7 +428,7 @@ TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, do
       const double h = fmax(1e-7 * fabs(y[j]), 1e-17);
       const double y1 = y[1] + ((j == 1) ? h : 0.0), y2 = y[2] + ((j == 2) ? h : 0.0);
       double xg = xe_g, tg = td_g, fx[3];
-      feval64(c, b, k, y1, y2, Kinv, xg, tg, fx);
+      feval64(c, b, k, y1, y2, Kinv, xg, tg, fx, nullptr, 1);
       const double sj = dts / h;
       for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - sj * (fx[i] - f0[i]);
     }
@@ -438,7 +438,7 @@ TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, do
       CoolT<double> kT = cool_T(c, bT, p.flags);
       double xg = xe_g, tg = td_g;
       double fT[3];
-      feval64(c, bT, kT, y[1], y[2], Kinv, xg, tg, fT);
+      feval64(c, bT, kT, y[1], y[2], Kinv, xg, tg, fT, nullptr, 1);
       const double s0 = dts / h;
       for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - s0 * (fT[i] - f0[i]);
     }

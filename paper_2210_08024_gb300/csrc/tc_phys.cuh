@@ -350,9 +350,9 @@ template <class F> struct Equil {
 // Electron balance g(x_e) = x_e - a0 - w x_C+(x_e) = 0 (Eqs. e:xEL / e:xELhot blended by
 // S(T), Eq. eq:C+_frac for x_C+), solved by Newton's method with the analytic derivative
 // inside the bracket [a0, a0 + w x_C,tot] (bisection when a step leaves it), warm-started
-// at `guess`, to a relative step of Prec<F>::root_tol.
+// at `guess`, to a relative step of Prec<F>::root_tol (or after newton_max Newton steps).
 template <class F> TCG_BIG Equil<F> equilibrium(const CellC<F>& c, const ChemT<F>& b, F xH2,
-                                                                  F xHp, F guess) {
+                                                                  F xHp, F guess, int newton_max = 100) {
   TCG_COUNT(equil);
   Equil<F> q;
   const F w = F(1) - b.S;
@@ -400,11 +400,16 @@ template <class F> TCG_BIG Equil<F> equilibrium(const CellC<F>& c, const ChemT<F
       F xn = x - g / gp;
       // a Newton step that lands on a bracket end is kept: near the root the bracket
       // collapses onto it, and bisecting there would only grind the bracket down
-      if (!(xn >= lo && xn <= hi)) xn = F(0.5) * (lo + hi);
+      const bool newton = (xn >= lo && xn <= hi);
+      if (!newton) xn = F(0.5) * (lo + hi);
       F dx = m_abs(xn - x);
       x = xn;
       xe = x;
       if (dx <= tol * x || hi - lo <= tol * hi) break;
+      // a caller whose guess is within ~1e-7 of the root (the Jacobian's perturbed
+      // evaluations, started from the base point's root) stops after newton_max Newton
+      // steps: one step from there is already converged to ~1e-14
+      if (newton && it + 1 >= newton_max) break;
     }
   }
   q.xe = xe;
