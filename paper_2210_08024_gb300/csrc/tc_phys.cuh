@@ -209,7 +209,7 @@ template <class F> TCG_FN CellC<F> cast_cell(const CellC<double>& d) {
 #define WDC6 1.333e-4
 
 template <class F> struct ChemT {
-  F T, lnT, sqT;
+  F T, lnT, sqT, invT;
   F S;                 // cooling/electron sigmoid of Sec. 4.3
   F kgr;               // Eq. e:H2form (or constant)
   F arr;               // case-B alpha_rr,H+
@@ -227,8 +227,9 @@ template <class F> TCG_BIG ChemT<F> chem_T(const CellC<F>& c, F T, unsigned flag
   b.T = T;
   b.lnT = m_log(T);
   b.sqT = m_sqrt(T);
-  F invT = F(1) / T;
-  b.S = F(1) / (F(1) + m_exp(F(-10.0) * (T - F(2.75e4)) / F(1.5e4)));
+  const F invT = F(1) / T;
+  b.invT = invT;
+  b.S = F(1) / (F(1) + m_exp(F(-10.0 / 1.5e4) * (T - F(2.75e4))));
   if (flags & FL_CONST_KGR) {
     b.kgr = F(3.0e-17) * c.Zd;
   } else {
@@ -246,8 +247,8 @@ template <class F> TCG_BIG ChemT<F> chem_T(const CellC<F>& c, F T, unsigned flag
   b.kCpH2 = F(4.0e-16) * m_exp(F(-0.2) * lT300);
   b.xMH_T = m_exp(F(0.345) * lT300) * F(2041.2414523193154);  // 1/sqrt(2.4e-7 (T/300)^-0.69)
   F lt = b.lnT * F(0.43429448190325176);  // log10 T
-  F xeHe = F(0.1) * (logistic((lt - F(4.45)) / F(0.06)) + logistic((lt - F(4.95)) / F(0.06)));
-  F xeMet = F(0.012) * logistic((lt - F(5.5)) / F(0.25));
+  F xeHe = F(0.1) * (logistic((lt - F(4.45)) * F(1.0 / 0.06)) + logistic((lt - F(4.95)) * F(1.0 / 0.06)));
+  F xeMet = F(0.012) * logistic((lt - F(5.5)) * F(4));
   b.xe_hot = xeHe + c.Zg * xeMet;
   b.wdH3T = F(WDH3) * m_exp(F(WDH4) * b.lnT);
   b.wdHex = F(-WDH5) - F(WDH6) * b.lnT;
@@ -275,7 +276,7 @@ template <class F> TCG_BIG CoolT<F> cool_T(const CellC<F>& c, const ChemT<F>& b,
   TCG_COUNT(cool_T);
   CoolT<F> k;
   const F T = b.T, lnT = b.lnT;
-  F invT = F(1) / T;
+  const F invT = b.invT;
   k.fcA = F(1.0e-12) * b.sqT * m_exp(F(-1000.0) * invT);
   k.fcB = F(1.4e-12) * b.sqT * m_exp(F(-18100.0) / (T + F(1200.0)));
   k.eps_num = F(5.22) + F(2.25) * m_exp(F(0.147) * lnT);
@@ -290,7 +291,7 @@ template <class F> TCG_BIG CoolT<F> cool_T(const CellC<F>& c, const ChemT<F>& b,
   k.ffrr = F(1.42e-27) * b.sqT * gff + b.arr * F(KB) * T * (F(0.684) - F(0.0416) * lT4);
   // C+ 158 um: n_e,crit = 53 T4^1/2, n_H,crit = 3e3 T2^(-0.1281 - 0.0087 ln T2), A = 2.3e-6
   F lT2 = lnT - F(4.605170185988092);
-  k.cpke = F(2.3e-6 / 53.0) / (b.sqT * F(0.01));
+  k.cpke = F(2.3e-6 / 53.0 * 100.0) * b.sqT * invT;  // / (53 T^1/2 / 100)
   k.cpkH = F(2.3e-6 / 3e3) * m_exp((F(0.1281) + F(0.0087) * lT2) * lT2);
   k.cpb = F(2) * m_exp(F(-91.25) * invT);
   // O 3-level: n_crit(T) through 2.5e5 (10 K) and 4.9e4 (5000 K); C: 620 and 150
@@ -316,7 +317,7 @@ template <class F> TCG_BIG CoolT<F> cool_T(const CellC<F>& c, const ChemT<F>& b,
     F poly = F(-103.0) + x * (F(97.59) + x * (F(-48.05) + x * (F(10.80) + x * F(-0.9032))));
     k.rvLlow = m_exp(poly * F(LN10));
     F lT3 = lnTc - F(6.907755278982137);
-    F iT3 = m_exp(-lT3);
+    F iT3 = F(1000) / m_min(m_max(T, F(10)), F(1e4));  // 1/T3 = exp(-lT3)
     F q = F(0.13) * iT3;
     F Lrot = F(9.5e-22) * m_exp(F(3.76) * lT3 - q * q * q) / (F(1) + F(0.12) * m_exp(F(2.1) * lT3)) +
              F(3e-24) * m_exp(F(-0.51) * iT3);
@@ -335,7 +336,7 @@ template <class F> TCG_BIG CoolT<F> cool_T(const CellC<F>& c, const ChemT<F>& b,
   if (flags & FL_NO_CIE) {
     k.cie = F(0);
   } else {
-    F z1 = (lt - F(5.0)) / F(0.15), z2 = (lt - F(5.35)) / F(0.28), z3 = (lt - F(6.3)) / F(0.35);
+    F z1 = (lt - F(5.0)) * F(1.0 / 0.15), z2 = (lt - F(5.35)) * F(1.0 / 0.28), z3 = (lt - F(6.3)) * F(1.0 / 0.35);
     k.cie = F(2.0e-23) * m_exp(F(-0.5) * z1 * z1) +
             c.Zg * (F(5.4e-22) * m_exp(F(-0.5) * z2 * z2) + F(5.0e-23) * m_exp(F(-0.5) * z3 * z3));
   }
@@ -372,14 +373,18 @@ template <class F> TCG_BIG Equil<F> equilibrium(const CellC<F>& c, const ChemT<F
     F pa = m_exp(F(WDC2) * lp);
     F pb = b.wdC3T * m_exp(b.wdCex * lp);
     F D = F(1) + F(WDC1) * pa * (F(1) + pb);
-    F agr = agr0 / D;
+    F invD = F(1) / D;
+    F agr = agr0 * invD;
     F den = sink0 + (agr + b.arrC * x) * c.n;
-    // d agr/d psi and d psi/d x (= -(psi - 50)/x when ne > floor)
-    F dD = F(WDC1) * (F(WDC2) * pa * (F(1) + pb) + pa * b.wdCex * pb) / psi;
-    F dpsi = (ne > F(1e-30)) ? -(psi - F(50)) / x : F(0);
-    F dagr = -agr0 * dD / (D * D) * dpsi;
-    F r = num / den;
-    dxcp = -r / den * ((dagr + b.arrC) * c.n);
+    // dD/dx = dD/dpsi dpsi/dx, with psi dD/dpsi = C1 (C2 pa (1 + pb) + pa C5' pb) and
+    // dpsi/dx = -(psi - 50)/x when ne > floor; d agr/dx = -agr dD/dx / D
+    F dDdx = (ne > F(1e-30))
+                 ? -F(WDC1) * (F(WDC2) * pa * (F(1) + pb) + pa * b.wdCex * pb) * (psi - F(50)) / (psi * x)
+                 : F(0);
+    F dagr = -agr * invD * dDdx;
+    F invden = F(1) / den;
+    F r = num * invden;
+    dxcp = -r * invden * ((dagr + b.arrC) * c.n);
     return r;
   };
   F lo = a0, hi = a0 + w * c.xCtot;
@@ -544,8 +549,13 @@ template <class F> TCG_BIG Src<F> source(const CellC<F>& c, const ChemT<F>& b, c
     // C+ two-level
     F C10 = n * (k.cpke * xe + k.cpkH * (xH + F(0.5) * xH2));
     F C01 = C10 * k.cpb;
-    Lmet = q.xCp * (C01 / (F(2.3e-6) + C10 + C01)) * F(2.3e-6 * 91.25 * KB) / n;
-    // O and C three-level atoms, H and H2 collisions (H2 at half the H rate)
+    // (energies in K; k_B and 1/n applied once at the end, which keeps the partial
+    // sums far above FP32's smallest normal number)
+    F lines = q.xCp * (C01 / (F(2.3e-6) + C10 + C01)) * F(2.3e-6 * 91.25);
+    // O and C three-level atoms, H and H2 collisions (H2 at half the H rate).  The level
+    // populations relative to the ground state are r1 = p1/det and r2 = p2/det, and the
+    // cooling per atom (r1 A1 E1 + r2 (A20 E2 + A21 E21)) / (1 + r1 + r2) is taken as
+    // (p1 A1 E1 + p2 (...)) / (det + p1 + p2), one quotient instead of three.
     F coll = n * (xH + F(0.5) * xH2);
     {
       F C10o = k.ok10 * coll;
@@ -554,11 +564,10 @@ template <class F> TCG_BIG Src<F> source(const CellC<F>& c, const ChemT<F>& b, c
       F bb = F(1.75e-5) + C10o;
       F a22 = F(1.34e-10) + F(1.75e-5) + F(2) * C10o;
       F det = a11 * a22 - bb * C12o;
-      F r1 = (C01o * a22 + bb * C02o) / det;
-      F r2 = (a11 * C02o + C12o * C01o) / det;
-      F z = F(1) + r1 + r2;
-      Lmet += q.xO * (r1 * F(8.91e-5 * 227.7) + r2 * F(1.34e-10 * 326.6 + 1.75e-5 * (326.6 - 227.7))) / z *
-              F(KB) / n;
+      F p1 = C01o * a22 + bb * C02o;
+      F p2 = a11 * C02o + C12o * C01o;
+      lines += q.xO * (p1 * F(8.91e-5 * 227.7) + p2 * F(1.34e-10 * 326.6 + 1.75e-5 * (326.6 - 227.7))) /
+               (det + p1 + p2);
     }
     {
       F C10c = k.ck10 * coll;
@@ -567,11 +576,12 @@ template <class F> TCG_BIG Src<F> source(const CellC<F>& c, const ChemT<F>& b, c
       F bb = F(2.65e-7) + C10c;
       F a22 = F(2.0e-14) + F(2.65e-7) + F(2) * C10c;
       F det = a11 * a22 - bb * C12c;
-      F r1 = (C01c * a22 + bb * C02c) / det;
-      F r2 = (a11 * C02c + C12c * C01c) / det;
-      F z = F(1) + r1 + r2;
-      Lmet += q.xC * (r1 * F(7.93e-8 * 23.6) + r2 * F(2.0e-14 * 62.4 + 2.65e-7 * (62.4 - 23.6))) / z * F(KB) / n;
+      F p1 = C01c * a22 + bb * C02c;
+      F p2 = a11 * C02c + C12c * C01c;
+      lines += q.xC * (p1 * F(7.93e-8 * 23.6) + p2 * F(2.0e-14 * 62.4 + 2.65e-7 * (62.4 - 23.6))) /
+               (det + p1 + p2);
     }
+    Lmet = lines * F(KB) / n;
     // CO (stand-in with LVG-like trapping)
     Lmet += q.xCO * k.coA / (F(1) + n / k.coN + q.xCO * c.NtX * F(1e-17));
     // grain-assisted recombination
