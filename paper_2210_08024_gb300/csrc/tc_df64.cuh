@@ -49,43 +49,104 @@
 namespace tcg {
 
 // ------------------------------------------------------------------ FP32 primitives
-// On the device the rounded intrinsics keep the compiler from contracting or
-// reassociating the error-free transformations (also in fast-math builds); on the host
-// the library is compiled without floating-point contraction.
+// On the device these are written as PTX instructions without the .ftz modifier: the
+// mixed kernels are built with flush-to-zero for their FP32 arithmetic, which would
+// flush every trailing part below 2^-126 (those of values below ~2e-31) and the
+// constants that small.  Written out, they keep subnormals, are never contracted or
+// reassociated, and df64 keeps its precision down to FP32's subnormal range.  On the
+// host the library is compiled without floating-point contraction or flushing.
 TCG_FN float df_add_rn(float a, float b) {
 #ifdef __CUDA_ARCH__
-  return __fadd_rn(a, b);
+  float r;
+  asm("add.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
 #else
   return a + b;
 #endif
 }
 TCG_FN float df_sub_rn(float a, float b) {
 #ifdef __CUDA_ARCH__
-  return __fsub_rn(a, b);
+  float r;
+  asm("sub.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
 #else
   return a - b;
 #endif
 }
 TCG_FN float df_mul_rn(float a, float b) {
 #ifdef __CUDA_ARCH__
-  return __fmul_rn(a, b);
+  float r;
+  asm("mul.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
 #else
   return a * b;
 #endif
 }
 TCG_FN float df_fma(float a, float b, float c) {
 #ifdef __CUDA_ARCH__
-  return __fmaf_rn(a, b, c);
+  float r;
+  asm("fma.rn.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
 #else
   return fmaf(a, b, c);
 #endif
 }
-// Correctly rounded FP32 reciprocal (the first quotient digit of a division).
+TCG_FN float df_neg(float a) {
+#ifdef __CUDA_ARCH__
+  float r;
+  asm("neg.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+#else
+  return -a;
+#endif
+}
+// FP32 quotient good to 2 units in the last place over the full range, subnormal
+// operands included (a quotient digit of the df64 division).
+TCG_FN float df_div(float a, float b) {
+#ifdef __CUDA_ARCH__
+  float r;
+  asm("div.full.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+#else
+  return a / b;
+#endif
+}
+// Correctly rounded FP32 reciprocal and an approximate square root, subnormals kept.
 TCG_FN float df_rcp(float a) {
 #ifdef __CUDA_ARCH__
-  return __frcp_rn(a);
+  float r;
+  asm("rcp.rn.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
 #else
   return 1.0f / a;
+#endif
+}
+TCG_FN float df_sqrt_approx(float a) {
+#ifdef __CUDA_ARCH__
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+#else
+  return sqrtf(a);
+#endif
+}
+// FP64 <-> FP32 conversions that keep subnormal FP32 values.
+TCG_FN float df_f64_to_f32(double x) {
+#ifdef __CUDA_ARCH__
+  float r;
+  asm("cvt.rn.f32.f64 %0, %1;" : "=f"(r) : "d"(x));
+  return r;
+#else
+  return float(x);
+#endif
+}
+TCG_FN double df_f32_to_f64(float x) {
+#ifdef __CUDA_ARCH__
+  double r;
+  asm("cvt.f64.f32 %0, %1;" : "=d"(r) : "f"(x));
+  return r;
+#else
+  return double(x);
 #endif
 }
 // 2^m for -126 <= m <= 127.
@@ -121,6 +182,8 @@ struct df64 {
   float hi, lo;
   df64() = default;
   // From FP64: the leading 48 bits, split exactly; magnitudes above DF_BIG saturate.
+  // For constants (evaluated at compile time); values computed at run time convert
+  // with to_df64, which keeps subnormal trailing parts on the device.
   TCG_FN constexpr df64(double x)
       : hi((x > DF_BIG) ? float(DF_BIG) : (x < -DF_BIG) ? float(-DF_BIG) : float(x)),
         lo((x > DF_BIG || x < -DF_BIG) ? 0.0f : float(x - double(float(x)))) {}
@@ -130,10 +193,18 @@ struct df64 {
     r.lo = l;
     return r;
   }
-  TCG_FN explicit operator double() const { return double(hi) + double(lo); }
+  TCG_FN explicit operator double() const { return df_f32_to_f64(hi) + df_f32_to_f64(lo); }
 };
 
-TCG_FN df64 operator-(df64 a) { return df64::make(-a.hi, -a.lo); }
+// Run-time conversion from FP64 (same result as the constructor, subnormals kept).
+TCG_FN df64 to_df64(double x) {
+  if (x > DF_BIG) return df64::make(float(DF_BIG), 0.0f);
+  if (x < -DF_BIG) return df64::make(float(-DF_BIG), 0.0f);
+  const float h = df_f64_to_f32(x);
+  return df64::make(h, df_f64_to_f32(x - df_f32_to_f64(h)));
+}
+
+TCG_FN df64 operator-(df64 a) { return df64::make(df_neg(a.hi), df_neg(a.lo)); }
 
 TCG_FN df64 operator+(df64 a, df64 b) {
   float s, e;
@@ -176,9 +247,9 @@ TCG_FN df64 add_f(df64 a, float b) {
 // The quotients are FP32 divisions, not products with a reciprocal: the reciprocal of
 // a subnormal divisor overflows, and 0 times it would give NaN where the quotient is 0.
 __host__ __device__ __noinline__ inline df64 operator/(df64 a, df64 b) {
-  const float q1 = a.hi / b.hi;
+  const float q1 = df_div(a.hi, b.hi);
   const df64 r = a - mul_f(b, q1);  // the remainder, ~2^-22 of a
-  const float q2 = r.hi / b.hi;
+  const float q2 = df_div(r.hi, b.hi);
   float h, l;
   fast_two_sum(q1, q2, h, l);
   return df64::make(h, l);
@@ -202,7 +273,7 @@ TCG_FN df64 m_min(df64 a, df64 b) { return (b < a) ? b : a; }
 
 __host__ __device__ __noinline__ inline df64 m_sqrt(df64 a) {
   if (!(a.hi > 0.0f)) return df64::make(sqrtf(a.hi), 0.0f);  // 0, or NaN below 0
-  const float s = sqrtf(a.hi);
+  const float s = df_sqrt_approx(a.hi);
   float p, e;
   two_prod(s, s, p, e);
   // (a - s^2) / (2 s) with a - s^2 formed exactly to first order (a.hi - p is exact)
@@ -277,7 +348,7 @@ __host__ __device__ __noinline__ inline df64 m_exp(df64 x) {
     two_prod(r.hi, r.hi, p, pe);
     pe = df_fma(2.0f * r.hi, r.lo, pe);
     float h, l;
-    fast_two_sum(0.5f * p, 0.5f * pe, h, l);
+    fast_two_sum(df_mul_rn(0.5f, p), df_mul_rn(0.5f, pe), h, l);
     em1 = r + df64::make(h, l);
     const float rh = r.hi;
     float q = df_fma(rh, 1.0f / 120.0f, 1.0f / 24.0f);
@@ -296,7 +367,7 @@ __host__ __device__ __noinline__ inline df64 m_exp(df64 x) {
   const df64 tj = df64::make(t.x, t.y);
   const df64 y = tj + tj * em1;
   const float sc = df_pow2i(m);
-  return df64::make(y.hi * sc, y.lo * sc);
+  return df64::make(df_mul_rn(y.hi, sc), df_mul_rn(y.lo, sc));
 }
 
 // log(x) for a df64 argument (method in the header comment), with x first scaled by a
@@ -313,7 +384,7 @@ __host__ __device__ __noinline__ inline df64 m_log(df64 x) {
   if (e > 126) e = 126;
   if (e < -126) e = -126;
   const float sc = df_pow2i(-e);
-  const df64 m = df64::make(x.hi * sc, x.lo * sc);
+  const df64 m = df64::make(df_mul_rn(x.hi, sc), df_mul_rn(x.lo, sc));
   const float y0 = logf(m.hi);
   const df64 d = add_f(m * m_exp(df64::make(-y0, 0.0f)), -1.0f);
   const float dh = d.hi;
@@ -326,7 +397,7 @@ __host__ __device__ __noinline__ inline df64 m_log(df64 x) {
   df64 eln2;
   {
     float s1, e1;
-    two_sum(fe * L1, p, s1, e1);
+    two_sum(df_mul_rn(fe, L1), p, s1, e1);
     e1 = df_add_rn(e1, df_add_rn(pe, df_mul_rn(fe, L3)));
     float h, l;
     fast_two_sum(s1, e1, h, l);

@@ -14,8 +14,8 @@ using tcg::df64;
 __global__ void k_df64_eval(int op, const double* __restrict__ a, const double* __restrict__ b,
                             double* __restrict__ out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const df64 x(a[i]);
-    const df64 y(b ? b[i] : 0.0);
+    const df64 x = tcg::to_df64(a[i]);
+    const df64 y = tcg::to_df64(b ? b[i] : 0.0);
     df64 r;
     switch (op) {
       case 0: r = x + y; break;
@@ -44,10 +44,10 @@ __global__ void __launch_bounds__(64) k_df64_source_check(tcg::DevFields f, tcg:
     const CoolT<double> k = cool_T(c, b, p.flags);
     const Equil<double> q = equilibrium(c, b, x2, xp, -1.0);
     const Src<double> s = source(c, b, k, x2, xp, xH, q, -1.0, -1.0);
-    const ChemT<df64> bd = chem_T(cd, df64(T), p.flags);
+    const ChemT<df64> bd = chem_T(cd, to_df64(T), p.flags);
     const CoolT<df64> kd = cool_T(cd, bd, p.flags);
-    const Equil<df64> qd = equilibrium(cd, bd, df64(x2), df64(xp), df64(-1.0));
-    const Src<df64> sd = source(cd, bd, kd, df64(x2), df64(xp), df64(xH), qd, df64(-1.0), df64(-1.0));
+    const Equil<df64> qd = equilibrium(cd, bd, to_df64(x2), to_df64(xp), df64(-1.0));
+    const Src<df64> sd = source(cd, bd, kd, to_df64(x2), to_df64(xp), to_df64(xH), qd, df64(-1.0), df64(-1.0));
     const double nn = c.n;
     err[i] = fabs(double(sd.H) - s.H) / (nn * fabs(s.G) + nn * nn * fabs(s.L));
     err[n + i] = fabs(double(sd.CH2) - s.CH2) / fmax(s.form + s.dest, 1e-300);
@@ -65,7 +65,7 @@ __global__ void k_df64_peak(int iters, double* sink) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   df64 v[CH];
 #pragma unroll
-  for (int c = 0; c < CH; ++c) v[c] = df64(0.5 + 1e-3 * (double)((tid + c) & 63));
+  for (int c = 0; c < CH; ++c) v[c] = tcg::to_df64(0.5 + 1e-3 * (double)((tid + c) & 63));
   const df64 a(0.999), b(1e-4);
   for (int i = 0; i < iters; ++i) {
 #pragma unroll

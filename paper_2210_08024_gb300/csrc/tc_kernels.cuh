@@ -233,9 +233,10 @@ TCG_FN void substep_paper(const CellC<double>& c, const DevParams& p, double dt,
 template <class F>
 TCG_FN void feval_t(const CellC<F>& c, const ChemT<F>& b, const CoolT<F>& k, double y1, double y2, double Kinv,
                     F& xe_guess, F& td_guess, double* f, Equil<F>* qout = nullptr, int eq_newton_max = 100) {
-  Equil<F> q = equilibrium(c, b, F(y1), F(y2), xe_guess, eq_newton_max);
+  const F fy1 = to_prec<F>(y1), fy2 = to_prec<F>(y2);
+  Equil<F> q = equilibrium(c, b, fy1, fy2, xe_guess, eq_newton_max);
   if (qout) *qout = q;
-  Src<F> s = source(c, b, k, F(y1), F(y2), F(1.0 - 2.0 * y1 - y2), q, F(-1.0), td_guess);
+  Src<F> s = source(c, b, k, fy1, fy2, to_prec<F>(1.0 - 2.0 * y1 - y2), q, F(-1.0), td_guess);
   xe_guess = q.xe;
   td_guess = s.Td;
   f[0] = double(s.H) * Kinv;
@@ -493,15 +494,16 @@ template <class F>
 TCG_FN void start_sources(const CellC<F>& cf, const DevParams& p, const LaneState& s, F& td_g, double& H0,
                           double& CH2, double& CHp, ChemT<F>* bo = nullptr, CoolT<F>* ko = nullptr) {
   const double T = s.mu * s.Tmu;
-  ChemT<F> b = chem_T(cf, F(T), p.flags);
+  ChemT<F> b = chem_T(cf, to_prec<F>(T), p.flags);
   CoolT<F> k = cool_T(cf, b, p.flags);
   if (bo) { *bo = b; *ko = k; }
   Equil<F> q;
-  q.xe = F(s.xe); q.xCp = F(s.xCp); q.xCO = F(s.xCO);
-  q.xOp = cf.xOtot * F(s.xHp);
+  q.xe = to_prec<F>(s.xe); q.xCp = to_prec<F>(s.xCp); q.xCO = to_prec<F>(s.xCO);
+  q.xOp = cf.xOtot * to_prec<F>(s.xHp);
   q.xC = cf.xCtot - q.xCp - q.xCO;
   q.xO = cf.xOtot - q.xCO - q.xOp;
-  Src<F> sr = source(cf, b, k, F(s.xH2), F(s.xHp), F(1.0 - 2.0 * s.xH2 - s.xHp), q, F(-1), td_g);
+  Src<F> sr = source(cf, b, k, to_prec<F>(s.xH2), to_prec<F>(s.xHp), to_prec<F>(1.0 - 2.0 * s.xH2 - s.xHp), q, F(-1),
+                     td_g);
   td_g = sr.Td;
   const double n = double(cf.n);
   H0 = n * double(sr.G) - n * n * double(sr.L);
@@ -940,13 +942,17 @@ TCG_FN int newton_mixed(const CellC<float>& cf, const DevParams& p, double mu, d
 // A chord iteration contracts by the Jacobian's relative error rho (~1e-3 there), so
 // after a correction d_k the remaining error is about rho d_k / (1 - rho), with rho
 // estimated as d_k / d_(k-1).  Accepted when that estimate is below 1e-9 relative
-// (abundances relative to max(x, 1e-4)), or when a single correction is below 1e-7;
+// (abundances relative to max(x, 1e-4)), or when a single correction is below 3e-8;
 // after at most five corrections, otherwise the FP64 solver takes the substep.
 // Measured on 4 x 4096 random-state cells, largest error in T against the FP64 oracle
 // after one step, and polish evaluations per slab substep:
 //   Jacobian from the FP32 iteration, single correction below 1e-8: 4.6e-6, 1.83
 //   (below 1e-7: 1.05e-5, 1.13, over the bound);
-//   Jacobian rebuilt at the FP32 root, single correction below 1e-7: 1.1e-6, 1.14.
+//   Jacobian rebuilt at the FP32 root, single correction below 1e-7: 1.1e-6, 1.15;
+//   below 3e-8: 1.48 evaluations.  On a PDR slab run for 120 steps of 1 Myr the
+//   largest error fell from 1.5e-6 (1e-7) to 1.1e-9 (3e-8; 1e-8 gave 1.2e-9): a
+//   correction just under 1e-7 left an error that the cold molecular gas amplified
+//   over the following steps.
 // `qlast` receives the C/O/e equilibrium of the last evaluation.
 template <class F>
 TCG_FN bool polish_hp(const CellC<F>& c, const DevParams& p, double mu, double Kinv, const double* yn, double dts,
@@ -954,7 +960,7 @@ TCG_FN bool polish_hp(const CellC<F>& c, const DevParams& p, double mu, double K
   double prev = -1.0;
   for (int it = 0; it < 5; ++it) {
     TCG_COUNT_D(polish_it);
-    ChemT<F> b = chem_T(c, F(mu * y[0]), p.flags);
+    ChemT<F> b = chem_T(c, to_prec<F>(mu * y[0]), p.flags);
     CoolT<F> k = cool_T(c, b, p.flags);
     double f0[3];
     feval_t<F>(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, &qlast);
@@ -976,7 +982,7 @@ TCG_FN bool polish_hp(const CellC<F>& c, const DevParams& p, double mu, double K
       prev = -1.0;
       continue;
     }
-    if (nrm <= 1e-7) return true;
+    if (nrm <= 3e-8) return true;
     if (prev > 0.0) {
       const double rho = nrm / prev;
       if (rho < 0.5 && rho * nrm <= 1e-9 * (1.0 - rho)) return true;
@@ -1173,8 +1179,8 @@ __global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_B
           // initial C/O/e equilibrium (it sets mu and hence T_mu): in df64 in the mixed
           // modes, whose FP64 physics then runs only in their rare fallbacks
           cd = cast_cell<df64>(c);
-          ChemT<df64> b0 = chem_T(cd, df64(T0), p.flags);
-          Equil<df64> q0 = equilibrium(cd, b0, df64(x20), df64(xp0), df64(-1.0));
+          ChemT<df64> b0 = chem_T(cd, to_df64(T0), p.flags);
+          Equil<df64> q0 = equilibrium(cd, b0, to_df64(x20), to_df64(xp0), df64(-1.0));
           s.xe = double(q0.xe); s.xCp = double(q0.xCp); s.xCO = double(q0.xCO);
           xe_g = s.xe;
           td_g = -1.0;

@@ -91,6 +91,11 @@ template <> struct Prec<df64> {
   static constexpr int cls = 2;
 };
 
+// A value computed at run time, in precision F (df64 keeps subnormal trailing parts on
+// the device; constants convert at compile time with F(x)).
+template <class F> TCG_FN F to_prec(double x) { return F(x); }
+template <> TCG_FN df64 to_prec<df64>(double x) { return to_df64(x); }
+
 template <class F> TCG_FN F logistic(F z) { return F(1) / (F(1) + m_exp(-z)); }
 
 // Parameters copied to the device by value with each launch.
@@ -183,11 +188,11 @@ TCG_FN CellC<double> make_cell(double n, double chi_pe, double chi_lw, double fh
 
 template <class F> TCG_FN CellC<F> cast_cell(const CellC<double>& d) {
   CellC<F> c;
-  c.n = F(d.n); c.lnn = F(d.lnn); c.G0 = F(d.G0); c.zpd = F(d.zpd); c.zpiH = F(d.zpiH); c.zpiH2 = F(d.zpiH2);
-  c.zpiC_rad = F(d.zpiC_rad); c.zcrC = F(d.zcrC); c.xi = F(d.xi); c.lnCOc = F(d.lnCOc); c.qH2 = F(d.qH2);
-  c.xCtot = F(d.xCtot); c.xOtot = F(d.xOtot); c.Zg = F(d.Zg); c.Zd = F(d.Zd); c.NtX = F(d.NtX); c.Gd = F(d.Gd);
-  c.Bd = F(d.Bd); c.Cgd = F(d.Cgd); c.Tc = F(d.Tc); c.Tc4 = F(d.Tc4); c.Td_hi = F(d.Td_hi);
-  c.xMH_pref = F(d.xMH_pref); c.K = F(d.K); c.muH = F(d.muH);
+  c.n = to_prec<F>(d.n); c.lnn = to_prec<F>(d.lnn); c.G0 = to_prec<F>(d.G0); c.zpd = to_prec<F>(d.zpd); c.zpiH = to_prec<F>(d.zpiH); c.zpiH2 = to_prec<F>(d.zpiH2);
+  c.zpiC_rad = to_prec<F>(d.zpiC_rad); c.zcrC = to_prec<F>(d.zcrC); c.xi = to_prec<F>(d.xi); c.lnCOc = to_prec<F>(d.lnCOc); c.qH2 = to_prec<F>(d.qH2);
+  c.xCtot = to_prec<F>(d.xCtot); c.xOtot = to_prec<F>(d.xOtot); c.Zg = to_prec<F>(d.Zg); c.Zd = to_prec<F>(d.Zd); c.NtX = to_prec<F>(d.NtX); c.Gd = to_prec<F>(d.Gd);
+  c.Bd = to_prec<F>(d.Bd); c.Cgd = to_prec<F>(d.Cgd); c.Tc = to_prec<F>(d.Tc); c.Tc4 = to_prec<F>(d.Tc4); c.Td_hi = to_prec<F>(d.Td_hi);
+  c.xMH_pref = to_prec<F>(d.xMH_pref); c.K = to_prec<F>(d.K); c.muH = to_prec<F>(d.muH);
   return c;
 }
 
