@@ -650,7 +650,7 @@ TCG_FN void feval32(const CellC<float>& cf, const ChemT<float>& b, const CoolT<f
 // iterations earlier.  With LPC = 4 the four evaluations are split over the cell's lanes.
 template <int LPC = 1>
 TCG_FN void fd_jacobian32(const CellC<float>& cf, const DevParams& p, double mu, double Kinv, double dts,
-                          const double* y, float xe_g, float td_g, float J[3][3], double* fbase = nullptr) {
+                          const double* y, float xe_g, float td_g, float J[3][3]) {
   const double h0 = 1e-3 * y[0];
   const double h1 = fmax(1e-3 * fabs(y[1]), 1e-12), h2 = fmax(1e-3 * fabs(y[2]), 1e-12);
   double f0[3], f1[3], f2[3], fT[3];
@@ -691,7 +691,6 @@ TCG_FN void fd_jacobian32(const CellC<float>& cf, const DevParams& p, double mu,
     J[i][1] = ((i == 1) ? 1.f : 0.f) - s1 * float(f1[i] - f0[i]);
     J[i][2] = ((i == 2) ? 1.f : 0.f) - s2 * float(f2[i] - f0[i]);
   }
-  if (fbase) { fbase[0] = f0[0]; fbase[1] = f0[1]; fbase[2] = f0[2]; }
 }
 
 // Seeded FP64 solve (mode 4): FP64 chord iterations from the seed with the FP32
@@ -1030,24 +1029,7 @@ TCG_FN void substep_mixed_solve(const CellC<double>& c, const CellC<df64>& cd, c
     if (polish) s.status |= ST_POLISH;
     y32[0] = y[0]; y32[1] = y[1]; y32[2] = y[2];
     have32 = true;
-    double f32[3];
-    fd_jacobian32<LPC>(cf, p, s.mu, Kinv, dts, y, xe_g, td_g, J, f32);
-    {
-      // one more FP32 step with the fresh Jacobian (its base point is f at the root):
-      // it removes what is left of the chord iteration's error, so that the polish
-      // starts nearer the root
-      float Jw[3][3], rhs[3], d32[3];
-      for (int i = 0; i < 3; ++i) {
-        rhs[i] = float(-(y[i] - yn[i] - dts * f32[i]));
-        for (int j = 0; j < 3; ++j) Jw[i][j] = J[i][j];
-      }
-      if (solve3<float>(Jw, rhs, d32)) {
-        const double d[3] = {double(d32[0]), double(d32[1]), double(d32[2])};
-        double st[3], ys[3] = {y[0], y[1], y[2]};
-        damped_step(ys, d, st);
-        if (finite3(ys[0], ys[1], ys[2])) { y[0] = ys[0]; y[1] = ys[1]; y[2] = ys[2]; }
-      }
-    }
+    fd_jacobian32<LPC>(cf, p, s.mu, Kinv, dts, y, xe_g, td_g, J);
     df64 xg = df64::make(xe_g, 0.0f), tg = df64::make(td_g, 0.0f);
     if (!polish_hp<df64>(cd, p, s.mu, Kinv, yn, dts, y, J, xg, tg, qlast)) it = -1;
   }
