@@ -1139,8 +1139,17 @@ constexpr int STEP_MIN_BLOCKS = 8;
 // registers per thread) spill less.
 constexpr int STEP_MIN_BLOCKS_COOP = 4;
 
+// The mixed kernels (modes 2, 3) are bound by latency rather than a pipe (instruction
+// fetch, dependent df64 chains), and more resident warps hide more of it than the extra
+// spills cost: 12 blocks per SM (40 registers per thread).  Measured on the 128^3 slab,
+// mixed / seeded mixed ms: 8 blocks 67.1 / 56.6, 10: 58.6 / 52.6, 12: 58.1 / 51.0,
+// 16: 57.9 / 52.7.
+constexpr int STEP_MIN_BLOCKS_MIXED = 12;
+
 template <int MODE, bool BATCH, int LPC = 1>
-__global__ void __launch_bounds__(128, (LPC == 1) ? STEP_MIN_BLOCKS : STEP_MIN_BLOCKS_COOP)
+__global__ void __launch_bounds__(128, (LPC == 1) ? ((MODE == 2 || MODE == 3) ? STEP_MIN_BLOCKS_MIXED
+                                                                              : STEP_MIN_BLOCKS)
+                                                  : STEP_MIN_BLOCKS_COOP)
     k_step(DevFields f1, const BoxTable* __restrict__ boxes, DevParams p, double dt, unsigned long long* cursor,
            long long ntotal, const MlpDev* __restrict__ mlp) {
   static_assert(LPC == 1 || ((MODE == 1 || MODE == 2) && !BATCH), "cooperative kernels: modes 1 and 2, one box");
