@@ -42,7 +42,8 @@ extern "C" {
 #define TC_MODE_PAPER_FP64 0   /* the paper's sequential update (Sec. 6.1), FP64 throughout */
 #define TC_MODE_NEWTON_FP64 1  /* coupled backward Euler on (T_mu, x_H2, x_H+) by Newton, FP64 */
 #define TC_MODE_MIXED 2        /* as TC_MODE_NEWTON_FP64: Newton iterations on FP32 source terms, FP64 residual,
-                                  update, closure x_H, substep length and a final FP64 polish of each root */
+                                  update and closure x_H; the substep length and a final polish of each
+                                  root from double-float (df64) source terms */
 #define TC_MODE_MIXED_SEEDED 3 /* as TC_MODE_MIXED, each Newton solve seeded by the MLP */
 #define TC_MODE_NEWTON_FP64_SEEDED 4 /* as TC_MODE_NEWTON_FP64, MLP-seeded */
 
@@ -57,7 +58,7 @@ extern "C" {
 #define TC_ST_NEWTON 2       /* a Newton solve failed and the substep was halved */
 #define TC_ST_NONFINITE 4
 #define TC_ST_FALLBACK 8     /* a mixed solve did not converge; the FP64 Newton finished that substep */
-#define TC_ST_POLISHED 16    /* a mixed solve stopped at the FP32 rounding floor before its FP64 polish */
+#define TC_ST_POLISHED 16    /* a mixed solve stopped at the FP32 rounding floor before its df64 polish */
 #define TC_ST_PREDICTOR 32   /* a Newton solve from the start state failed and was restarted from the
                                  block predictor (abundances by the 2x2 backward Euler, then T) */
 #define TC_ST_SEEDED 64      /* seeded modes: a substep's solve started from the seed network converged */
@@ -80,7 +81,7 @@ typedef struct tc_params {
   int mode;                    /* TC_MODE_* */
   unsigned flags;              /* TC_CONST_KGR | TC_NO_ROVIB | TC_NO_CIE */
   double newton_rtol_mixed;    /* step tolerance of the FP32 Newton iterations of the mixed modes; default 1e-6
-                                  (the FP64 polish then brings each root to ~1e-9 relative) */
+                                  (the df64 polish then brings each root to ~1e-9 relative) */
   int block;                   /* threads per block (0 = autotuned/default) */
   int blocks_per_sm;           /* resident blocks per SM for the persistent grid (0 = occupancy) */
   int order_cells;             /* 1 (default): hand cells to the persistent kernel in decreasing order of

@@ -263,12 +263,13 @@ static int coop_occupancy(int kmode, int block) {
 
 // Launch shape of one step launch: threads per block, grid and lanes per cell.  Explicit
 // tc_params values win; otherwise the shape tc_autotune recorded for the launch's size
-// class; otherwise 128 threads, the occupancy limit, and for mode 1 four lanes per cell
-// when every cell's four lanes fit the cooperative kernel's resident lanes at once
-// (4096 random states: 110 ms against 176 ms with one lane).  The mixed mode builds its
-// Jacobian once per solve and spends its time in the FP64 polish, which four lanes do
-// not shorten (108 against 98 ms), so it keeps one lane unless tuned.  The persistent
-// grid never exceeds the blocks that hold one lane per cell lane.
+// class; otherwise 128 threads, the occupancy limit, and for modes 1 and 2 four lanes per
+// cell when every cell's four lanes fit the cooperative kernel's resident lanes at once
+// (4096 random states: FP64 Newton 96.9 ms against 139.1 ms with one lane, mixed 45.1
+// against 48.8 ms; the mixed solve builds one FP32 Jacobian per solve and spends most of
+// its time in the df64 polish and substep-start sources, which four lanes do not
+// shorten).  The persistent grid never exceeds the blocks that hold one lane per cell
+// lane.
 struct Shape {
   int grid, block, lpc;
 };
@@ -286,7 +287,7 @@ static Shape launch_shape(tc_handle* h, int kmode, bool batch, long long ntotal)
   b = (b / 32) * 32;
   if (b < 32) b = 32;
   if (!coop_ok) lpc = 1;
-  if (lpc <= 0) lpc = (kmode == 1 && ntotal * 4 <= (long long)h->num_sms * coop_occupancy(kmode, b) * b) ? 4 : 1;
+  if (lpc <= 0) lpc = (coop_ok && ntotal * 4 <= (long long)h->num_sms * coop_occupancy(kmode, b) * b) ? 4 : 1;
   if (lpc != 4) lpc = 1;
   if (per_sm <= 0) {
     per_sm = (lpc == 4) ? coop_occupancy(kmode, b)

@@ -655,7 +655,7 @@ TCG_FN void feval32(const CellC<float>& cf, const ChemT<float>& b, const CoolT<f
 }
 
 // FP32 forward-difference Jacobian (relative step 1e-3) of the backward-Euler residual
-// at y, built afresh at the FP32 iteration's root before the FP64 polish: at the root
+// at y, built afresh at the FP32 iteration's root before the df64 polish: at the root
 // itself it is as good as an FP32 difference gets (~1e-3), so the polish contracts by
 // about that much per correction instead of by the error of a Jacobian built several
 // iterations earlier.  With LPC = 4 the four evaluations are split over the cell's lanes.

@@ -14,7 +14,7 @@ scalar type; its counts per iteration are stated here from the code:
                                                       21 add, 15 mul, 9 div)
     mixed Newton iteration  18 add, 12 mul,  6 div   (its FP64 part: residual, damped step
                                                       and test; the correction is solved in FP32)
-    FP64 polish iteration   16 add, 12 mul,  6 div   (the same with the FP64 residual)
+    polish iteration        16 add, 12 mul,  6 div   (the same, residual from df64 sources)
     paper-scheme substep    18 add, 18 mul,  8 div   (FD slope, T update, 2x2 solve)
     predictor sweep         30 add, 30 mul,  8 div   (2x2 closed form, T step, change)
 
