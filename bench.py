@@ -45,12 +45,12 @@ FP64_NOMINAL_TFLOPS = 1.25
 STATE_KEYS = ("T", "xH2", "xHp")
 # DRAM bytes per cell of one k_step<1> launch on the 128^3 slab at the benchmark's
 # occupancy (1024 threads per SM), from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, one pass, profiles/k_step_fp64_slab128.md): 41.45 GB read +
-# 39.78 GB written for 2,097,152 cells.  Almost all of it is the per-thread stack (the
-# 64-register cap's spills and the structs passed to the out-of-line physics): 3.4 KB
-# per thread for 1024 resident threads per SM is ~530 MB, four times L2; at the
-# kernel's speed ~350 GB/s, 5% of HBM.  The cells' own data are 152 B.
-TRAFFIC_BYTES_PER_CELL = 38732.0
+# dram__bytes_write.sum, one pass, profiles/k_step_fp64_slab128.md); None while the
+# kernel has changed since the last capture.  Almost all of it is the per-thread stack
+# (the 64-register cap's spills and the structs passed to the out-of-line physics):
+# 3.4 KB per thread for 1024 resident threads per SM is ~530 MB, four times L2.  The
+# cells' own data are 152 B.
+TRAFFIC_BYTES_PER_CELL = None
 
 
 def parse():
@@ -643,7 +643,8 @@ def roofline_of(work, r, mode, ncell, peaks):
     achieved = fl / (r["kernel_ms"] * 1e-3) / 1e12
     peak = 2.0 * peaks["fp64_fma_per_s"] / 1e12
     return {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_CELL * ncell if mode == "newton" else None,
+            "frac": achieved / peak, "traffic": (TRAFFIC_BYTES_PER_CELL * ncell
+                                           if mode == "newton" and TRAFFIC_BYTES_PER_CELL else None),
             "peak_source": "measured FP64 FMA rate (library microbenchmark, this run); nominal %.2f" %
                            FP64_NOMINAL_TFLOPS,
             "work": "FP64 flops of the library's step per cell (work_slab128.json, %s) x %d cells" %
