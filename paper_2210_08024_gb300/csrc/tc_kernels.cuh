@@ -185,6 +185,7 @@ TCG_FN void substep_paper(const CellC<double>& c, const DevParams& p, double dt,
     q.xOp = c.xOtot * s.xHp;
     q.xC = c.xCtot - s.xCp - s.xCO;
     q.xO = c.xOtot - s.xCO - q.xOp;
+    q.lpsi = log_psi(c, b, q.xe);
     Src<double> sr = source(c, b, k, s.xH2, s.xHp, 1.0 - 2.0 * s.xH2 - s.xHp, q, Tdf, s.Td);
     if (pass == 0) { H0 = sr.H; CH2 = sr.CH2; CHp = sr.CHp; Td0 = sr.Td; }
     else Hp = sr.H;
@@ -254,7 +255,7 @@ template <class F>
 TCG_FN Equil<double> equil64(const Equil<F>& q) {
   Equil<double> r;
   r.xe = double(q.xe); r.xCp = double(q.xCp); r.xCO = double(q.xCO); r.xC = double(q.xC);
-  r.xO = double(q.xO); r.xOp = double(q.xOp); r.xMHp = double(q.xMHp);
+  r.xO = double(q.xO); r.xOp = double(q.xOp); r.xMHp = double(q.xMHp); r.lpsi = double(q.lpsi);
   return r;
 }
 
@@ -513,6 +514,7 @@ TCG_FN void start_sources(const CellC<F>& cf, const DevParams& p, const LaneStat
   q.xOp = cf.xOtot * to_prec<F>(s.xHp);
   q.xC = cf.xCtot - q.xCp - q.xCO;
   q.xO = cf.xOtot - q.xCO - q.xOp;
+  q.lpsi = log_psi(cf, b, q.xe);
   Src<F> sr = source(cf, b, k, to_prec<F>(s.xH2), to_prec<F>(s.xHp), to_prec<F>(1.0 - 2.0 * s.xH2 - s.xHp), q, F(-1),
                      td_g);
   td_g = sr.Td;
@@ -579,7 +581,7 @@ TCG_FN void picard_predictor(const CellC<double>& c, const DevParams& p, double 
     ChemT<double> b = chem_T(c, mu * y[0], p.flags);
     const Equil<double> q = equilibrium(c, b, y[1], y[2], xe_g);
     xe_g = q.xe;
-    const HRate<double> r = h_rates(c, b, y[1], 1.0 - 2.0 * y[1] - y[2], q.xe, log_psi(c, b, q.xe));
+    const HRate<double> r = h_rates(c, b, y[1], 1.0 - 2.0 * y[1] - y[2], q.xe, q.lpsi);
     const double a = 2.0 * r.kn + r.DH2;
     const double cc = r.I + r.Rr;
     const double det = 1.0 + (a + cc) * dts + (2.0 * r.kn * r.Rr + r.DH2 * cc) * dts * dts;

@@ -135,7 +135,7 @@ template <class F> struct CellC {
   F zpiH, zpiH2;        // 3.1e-18 F, 4.6e-18 F (Eqs. e:H_pi, eq:H2_pi)
   F zpiC_rad, zcrC;     // 3.43e-10 chi_LW f_shld,C ; 3.85 xi (Sec. 3.2.1)
   F xi;
-  F lnCOc;              // ln n_CO,crit (Eq. e:CO_fit), +inf without CRs or dust
+  F rCO2;               // (n_CO,crit / n)^2 (Eqs. e:CO, e:CO_fit), +inf without CRs or dust
   F qH2;                // q_cr,H2(n) in erg
   F xCtot, xOtot, Zg, Zd;
   F NtX;                // n_H / |dv/dr| [cm^-2 (km/s)^-1]
@@ -168,9 +168,10 @@ TCG_FN CellC<double> make_cell(double n, double chi_pe, double chi_lw, double fh
     double xi16 = xi * 1e16;
     double lnZd = log(Zd);
     double chi13 = (chi_lw > 0.0) ? exp(log(chi_lw) / 3.0) : 0.0;
-    c.lnCOc = chi13 * (log(4e3) + lnZd - 2.0 * log(xi16)) + (log(50.0 * xi16) - 1.4 * lnZd);
+    double lnCOc = chi13 * (log(4e3) + lnZd - 2.0 * log(xi16)) + (log(50.0 * xi16) - 1.4 * lnZd);
+    c.rCO2 = exp(2.0 * (lnCOc - c.lnn));
   } else {
-    c.lnCOc = INFINITY;
+    c.rCO2 = INFINITY;
   }
   double l10n = c.lnn / LN10;  // q_cr,H2: 10 -> 13 -> 17 -> 18 eV, linear in log10 n
   double q = (l10n < 2.0) ? 10.0
@@ -206,7 +207,7 @@ TCG_FN CellC<double> make_cell(double n, double chi_pe, double chi_lw, double fh
 template <class F> TCG_FN CellC<F> cast_cell(const CellC<double>& d) {
   CellC<F> c;
   c.n = to_prec<F>(d.n); c.lnn = to_prec<F>(d.lnn); c.G0 = to_prec<F>(d.G0); c.zpd = to_prec<F>(d.zpd); c.zpiH = to_prec<F>(d.zpiH); c.zpiH2 = to_prec<F>(d.zpiH2);
-  c.zpiC_rad = to_prec<F>(d.zpiC_rad); c.zcrC = to_prec<F>(d.zcrC); c.xi = to_prec<F>(d.xi); c.lnCOc = to_prec<F>(d.lnCOc); c.qH2 = to_prec<F>(d.qH2);
+  c.zpiC_rad = to_prec<F>(d.zpiC_rad); c.zcrC = to_prec<F>(d.zcrC); c.xi = to_prec<F>(d.xi); c.rCO2 = to_prec<F>(d.rCO2); c.qH2 = to_prec<F>(d.qH2);
   c.xCtot = to_prec<F>(d.xCtot); c.xOtot = to_prec<F>(d.xOtot); c.Zg = to_prec<F>(d.Zg); c.Zd = to_prec<F>(d.Zd); c.NtX = to_prec<F>(d.NtX); c.Gd = to_prec<F>(d.Gd);
   c.Bd = to_prec<F>(d.Bd); c.Cgd = to_prec<F>(d.Cgd); c.Tc = to_prec<F>(d.Tc); c.Tc4 = to_prec<F>(d.Tc4); c.Td_hi = to_prec<F>(d.Td_hi);
   c.xMH_pref = to_prec<F>(d.xMH_pref); c.K = to_prec<F>(d.K); c.muH = to_prec<F>(d.muH);
@@ -372,6 +373,7 @@ template <class F> TCG_BIG CoolT<F> cool_T(const CellC<F>& c, const ChemT<F>& b,
 // ------------------------------------------------------------------ C/O/e equilibrium (Secs. 3.2, 3.3)
 template <class F> struct Equil {
   F xe, xCp, xCO, xC, xO, xOp, xMHp;
+  F lpsi;  // ln psi at x_e, psi = G0 sqrt(T) / n_e + 50 (grain-charging parameter)
 };
 
 // Electron balance g(x_e) = x_e - a0 - w x_C+(x_e) = 0 (Eqs. e:xEL / e:xELhot blended by
@@ -392,10 +394,10 @@ template <class F> TCG_BIG Equil<F> equilibrium(const CellC<F>& c, const ChemT<F
   const F Gs = c.G0 * b.sqT;
   const F agr0 = F(1e-14 * WDC0) * c.Zd;
   // x_C+(x) and its derivative
-  auto xcp = [&](F x, F& dxcp) -> F {
+  auto xcp = [&](F x, F& dxcp, F& lp) -> F {
     F ne = x * c.n;
     F psi = Gs / m_max(ne, F(1e-30)) + F(50);
-    F lp = m_log(psi);
+    lp = m_log(psi);
     F pa = m_exp(F(WDC2) * lp);
     F pb = b.wdC3T * m_exp(b.wdCex * lp);
     F D = F(1) + F(WDC1) * pa * (F(1) + pb);
@@ -423,8 +425,8 @@ template <class F> TCG_BIG Equil<F> equilibrium(const CellC<F>& c, const ChemT<F
     xe = x;
     for (int it = 0; it < 100; ++it) {
       TCG_COUNT(equil_it);
-      F d;
-      F g = x - a0 - w * xcp(x, d);
+      F d, lpx;
+      F g = x - a0 - w * xcp(x, d, lpx);
       if (g == F(0)) { xe = x; break; }
       if (g > F(0)) hi = x; else lo = x;
       F gp = F(1) - w * d;
@@ -444,11 +446,12 @@ template <class F> TCG_BIG Equil<F> equilibrium(const CellC<F>& c, const ChemT<F
     }
   }
   q.xe = xe;
+  // the final evaluation's ln psi is log_psi(c, b, xe) to the bit (same operations):
+  // source() takes it from here
   F dd;
-  q.xCp = xcp(xe, dd);
+  q.xCp = xcp(xe, dd, q.lpsi);
   F fr = m_max((c.xCtot > F(0)) ? q.xCp / c.xCtot : F(0), xHp);
-  F r2 = m_exp(F(2) * (c.lnCOc - c.lnn));
-  q.xCO = c.xCtot * F(2) * xH2 * (F(1) - fr) / (F(1) + r2);  // Eq. e:CO
+  q.xCO = c.xCtot * F(2) * xH2 * (F(1) - fr) / (F(1) + c.rCO2);  // Eq. e:CO
   q.xC = c.xCtot - q.xCp - q.xCO;
   q.xO = c.xOtot - q.xCO - q.xOp;
   return q;
@@ -537,7 +540,7 @@ template <class F> TCG_BIG Src<F> source(const CellC<F>& c, const ChemT<F>& b, c
   Src<F> s;
   const F n = c.n;
   const F xe = q.xe;
-  const F lp = log_psi(c, b, xe);
+  const F lp = q.lpsi;  // log_psi(c, b, xe), from the equilibrium solve
   const HRate<F> r = h_rates(c, b, xH2, xH, xe, lp);
   s.form = r.kn * xH;
   s.dest = r.DH2 * xH2;
