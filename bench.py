@@ -43,14 +43,14 @@ UNIT = "cell-updates/s"
 FP64_NOMINAL_TFLOPS = 1.25
 
 STATE_KEYS = ("T", "xH2", "xHp")
-# DRAM bytes per cell of one k_step<1> launch on the 128^3 slab at the benchmark's
-# occupancy (1024 threads per SM), from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, one pass, profiles/k_step_fp64_slab128.md); None while the
-# kernel has changed since the last capture.  Almost all of it is the per-thread stack
-# (the 64-register cap's spills and the structs passed to the out-of-line physics):
-# 3.4 KB per thread for 1024 resident threads per SM is ~530 MB, four times L2.  The
-# cells' own data are 152 B.
-TRAFFIC_BYTES_PER_CELL = None
+# DRAM bytes per cell of one k_step<1> launch on the 128^3 slab in the autotuned shape
+# (64 threads x 1824 blocks, 768 resident threads per SM), from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, one pass,
+# profiles/k_step_fp64_slab128.md): 24.38 GB read + 32.78 GB written for 2,097,152
+# cells.  Almost all of it is the per-thread stack (spills at the 80-register cap and
+# the structs passed to the out-of-line physics): 3.3 KB per thread for 768 resident
+# threads per SM is ~390 MB, three times L2.  The cells' own data are 152 B.
+TRAFFIC_BYTES_PER_CELL = 27252.0
 
 
 def parse():

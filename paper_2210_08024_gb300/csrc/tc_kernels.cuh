@@ -1135,7 +1135,13 @@ TCG_FN bool seed_from_outputs(const float* o, const double* g, const LaneState& 
 //   3 blocks (168 registers, compiler's choice) 546 / 403
 //   4 blocks (128) 394 / 195,  5 (96) 375 / 174,  6 (80) 365 / 164,
 //   7 (72) 362 / 156,  8 (64) 363 / 152.
+// With the FP64 exp and log out of line (a shorter per-thread stack) the autotuner picks
+// 4 resident blocks of 128 for FP64 Newton and the paper scheme, and their kernels are
+// compiled for 6 (80 registers): FP64 Newton 214.6 -> 212.9 ms, paper scheme 50.9 ->
+// 50.0 (4 blocks: 214.1 / 50.7, 5: 213.3 / 50.3).  The seeded FP64 kernel keeps 8
+// (293.5 ms; 300.1 at 6).
 constexpr int STEP_MIN_BLOCKS = 8;
+constexpr int STEP_MIN_BLOCKS_FP64 = 6;
 // The warp-cooperative kernels (four lanes per cell) serve launches too small to fill
 // the GPU, where the time is the latency of the slowest cells: 4 resident blocks (128
 // registers per thread) spill less.
@@ -1150,6 +1156,7 @@ constexpr int STEP_MIN_BLOCKS_MIXED = 12;
 
 template <int MODE, bool BATCH, int LPC = 1>
 __global__ void __launch_bounds__(128, (LPC == 1) ? ((MODE == 2 || MODE == 3) ? STEP_MIN_BLOCKS_MIXED
+                                                      : (MODE == 0 || MODE == 1) ? STEP_MIN_BLOCKS_FP64
                                                                               : STEP_MIN_BLOCKS)
                                                   : STEP_MIN_BLOCKS_COOP)
     k_step(DevFields f1, const BoxTable* __restrict__ boxes, DevParams p, double dt, unsigned long long* cursor,
