@@ -376,56 +376,62 @@ TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, do
                        double& rel, bool& full, Equil<double>* qb,
                        const ChemT<double>* b0 = nullptr, const CoolT<double>* k0 = nullptr) {
   double f0[3], J[3][3];
-  if (reuse) {
-    TCG_COUNT_D(chord64_it);
-    ChemT<double> b = chem_T(c, mu * y[0], p.flags);
-    CoolT<double> k = cool_T(c, b, p.flags);
-    feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, qb);
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) J[i][j] = Jk[i][j];
-  } else if constexpr (LPC == 4) {
-    TCG_COUNT_D(newton64_it);
-    // Warp-cooperative forward-difference Jacobian: lane q of the cell evaluates f at the
-    // base point (q = 0) or with x_H2 (q = 1), x_H+ (q = 2) or T_mu (q = 3) perturbed,
-    // each from the same x_e and T_d guesses; the four results are exchanged.
-    const int q = lane_in_cell<4>();
-    const double h0 = 1e-7 * y[0];
-    const double h1 = fmax(1e-7 * fabs(y[1]), 1e-17), h2 = fmax(1e-7 * fabs(y[2]), 1e-17);
-    double fq[3];
-    Equil<double> qq;
-    double xg = xe_g, tg = td_g;
-    {
-      ChemT<double> b = chem_T(c, mu * ((q == 3) ? y[0] + h0 : y[0]), p.flags);
+  if constexpr (LPC == 4) {
+    if (reuse) {
+      TCG_COUNT_D(chord64_it);
+      ChemT<double> b = chem_T(c, mu * y[0], p.flags);
       CoolT<double> k = cool_T(c, b, p.flags);
-      feval64(c, b, k, y[1] + ((q == 1) ? h1 : 0.0), y[2] + ((q == 2) ? h2 : 0.0), Kinv, xg, tg, fq, &qq);
-    }
-    const double s0 = dts / h0, s1 = dts / h1, s2 = dts / h2;
+      feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, qb);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) J[i][j] = Jk[i][j];
+    } else {
+      TCG_COUNT_D(newton64_it);
+      // Warp-cooperative forward-difference Jacobian: lane q of the cell evaluates f at the
+      // base point (q = 0) or with x_H2 (q = 1), x_H+ (q = 2) or T_mu (q = 3) perturbed,
+      // each from the same x_e and T_d guesses; the four results are exchanged.
+      const int q = lane_in_cell<4>();
+      const double h0 = 1e-7 * y[0];
+      const double h1 = fmax(1e-7 * fabs(y[1]), 1e-17), h2 = fmax(1e-7 * fabs(y[2]), 1e-17);
+      double fq[3];
+      Equil<double> qq;
+      double xg = xe_g, tg = td_g;
+      {
+        ChemT<double> b = chem_T(c, mu * ((q == 3) ? y[0] + h0 : y[0]), p.flags);
+        CoolT<double> k = cool_T(c, b, p.flags);
+        feval64(c, b, k, y[1] + ((q == 1) ? h1 : 0.0), y[2] + ((q == 2) ? h2 : 0.0), Kinv, xg, tg, fq, &qq);
+      }
+      const double s0 = dts / h0, s1 = dts / h1, s2 = dts / h2;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      f0[i] = from_lane<4>(fq[i], 0);
-      const double f1 = from_lane<4>(fq[i], 1), f2 = from_lane<4>(fq[i], 2), fT = from_lane<4>(fq[i], 3);
-      J[i][1] = ((i == 1) ? 1.0 : 0.0) - s1 * (f1 - f0[i]);
-      J[i][2] = ((i == 2) ? 1.0 : 0.0) - s2 * (f2 - f0[i]);
-      J[i][0] = ((i == 0) ? 1.0 : 0.0) - s0 * (fT - f0[i]);
+      for (int i = 0; i < 3; ++i) {
+        f0[i] = from_lane<4>(fq[i], 0);
+        const double f1 = from_lane<4>(fq[i], 1), f2 = from_lane<4>(fq[i], 2), fT = from_lane<4>(fq[i], 3);
+        J[i][1] = ((i == 1) ? 1.0 : 0.0) - s1 * (f1 - f0[i]);
+        J[i][2] = ((i == 2) ? 1.0 : 0.0) - s2 * (f2 - f0[i]);
+        J[i][0] = ((i == 0) ? 1.0 : 0.0) - s0 * (fT - f0[i]);
+      }
+      xe_g = from_lane<4>(xg, 0);
+      td_g = from_lane<4>(tg, 0);
+      if (qb) {
+        qb->xe = from_lane<4>(qq.xe, 0);
+        qb->xCp = from_lane<4>(qq.xCp, 0);
+        qb->xCO = from_lane<4>(qq.xCO, 0);
+      }
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Jk[i][j] = J[i][j];
     }
-    xe_g = from_lane<4>(xg, 0);
-    td_g = from_lane<4>(tg, 0);
-    if (qb) {
-      qb->xe = from_lane<4>(qq.xe, 0);
-      qb->xCp = from_lane<4>(qq.xCp, 0);
-      qb->xCO = from_lane<4>(qq.xCO, 0);
-    }
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) Jk[i][j] = J[i][j];
   } else {
-    TCG_COUNT_D(newton64_it);
-    // evaluation order: base point, x_H2 column, x_H+ column (all at the base T), then
-    // the T_mu column, so the temperature blocks are built twice per iteration.  The
-    // columns start their C/O/e and dust-temperature solves from the base point's roots,
-    // ~1e-7 away, and take one Newton step of the C/O/e balance (converged to ~1e-14
-    // from there; the loop would take a second to confirm it).  The temperature blocks
-    // at the base point are given by the caller at a substep's first iteration (the
-    // substep start's, the same temperature), else built here.
+    // One lane per cell: the base point is evaluated by every lane of the warp on one
+    // path, whether the lane then reuses its Jacobian (chord iteration) or rebuilds it,
+    // so a warp whose lanes mix the two runs the base evaluation once, not once per
+    // branch.  Rebuild order: base point, x_H2 column, x_H+ column (all at the base T),
+    // then the T_mu column from the base point's temperature blocks stepped to T + dT
+    // (temp_blocks_step).  The columns start their C/O/e and dust-temperature solves from the base
+    // point's roots, ~1e-7 away, and take one Newton step of the C/O/e balance
+    // (converged to ~1e-14 from there; the loop would take a second to confirm it).  The
+    // temperature blocks at the base point are given by the caller at a substep's first
+    // iteration (the substep start's, the same temperature), else built here.
+    if (reuse) TCG_COUNT_D(chord64_it);
+    else TCG_COUNT_D(newton64_it);
     ChemT<double> b;
     CoolT<double> k;
     if (b0) {
@@ -436,27 +442,35 @@ TCG_FN int newton_iter(const CellC<double>& c, const DevParams& p, double mu, do
       k = cool_T(c, b, p.flags);
     }
     feval64(c, b, k, y[1], y[2], Kinv, xe_g, td_g, f0, qb);
+    if (reuse) {
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) J[i][j] = Jk[i][j];
+    } else {
 #pragma unroll 1
-    for (int j = 1; j < 3; ++j) {
-      const double h = fmax(1e-7 * fabs(y[j]), 1e-17);
-      const double y1 = y[1] + ((j == 1) ? h : 0.0), y2 = y[2] + ((j == 2) ? h : 0.0);
-      double xg = xe_g, tg = td_g, fx[3];
-      feval64(c, b, k, y1, y2, Kinv, xg, tg, fx, nullptr, 1);
-      const double sj = dts / h;
-      for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - sj * (fx[i] - f0[i]);
+      for (int j = 1; j < 3; ++j) {
+        const double h = fmax(1e-7 * fabs(y[j]), 1e-17);
+        const double y1 = y[1] + ((j == 1) ? h : 0.0), y2 = y[2] + ((j == 2) ? h : 0.0);
+        double xg = xe_g, tg = td_g, fx[3];
+        feval64(c, b, k, y1, y2, Kinv, xg, tg, fx, nullptr, 1);
+        const double sj = dts / h;
+        for (int i = 0; i < 3; ++i) J[i][j] = ((i == j) ? 1.0 : 0.0) - sj * (fx[i] - f0[i]);
+      }
+      {
+        // the temperature blocks at T + dT stepped from the base point's (first order in
+        // dT = 1e-7 T: the same column to the difference's truncation error)
+        double h = 1e-7 * y[0];
+        ChemT<double> bT;
+        CoolT<double> kT;
+        temp_blocks_step(c, b, k, mu * (y[0] + h), p.flags, bT, kT);
+        double xg = xe_g, tg = td_g;
+        double fT[3];
+        feval64(c, bT, kT, y[1], y[2], Kinv, xg, tg, fT, nullptr, 1);
+        const double s0 = dts / h;
+        for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - s0 * (fT[i] - f0[i]);
+      }
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Jk[i][j] = J[i][j];
     }
-    {
-      double h = 1e-7 * y[0];
-      ChemT<double> bT = chem_T(c, mu * (y[0] + h), p.flags);
-      CoolT<double> kT = cool_T(c, bT, p.flags);
-      double xg = xe_g, tg = td_g;
-      double fT[3];
-      feval64(c, bT, kT, y[1], y[2], Kinv, xg, tg, fT, nullptr, 1);
-      const double s0 = dts / h;
-      for (int i = 0; i < 3; ++i) J[i][0] = ((i == 0) ? 1.0 : 0.0) - s0 * (fT[i] - f0[i]);
-    }
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) Jk[i][j] = J[i][j];
   }
   double rhs[3], d[3];
   for (int i = 0; i < 3; ++i) rhs[i] = -(y[i] - yn[i] - dts * f0[i]);

@@ -244,6 +244,16 @@ template <class F> struct ChemT {
   F wdH3T, wdHex, wdC3T, wdCex;  // C3 T^C4 and -C5 - C6 ln T for H and C
 };
 
+// Electrons of hot gas at log10 T = lt: x_e,He,CIE (two logistic steps, at 4.45 and
+// 4.95, whose exponentials differ by the constant factor exp(0.5/0.06)) + Z'_g
+// x_e,metal,CIE (one step at 5.5).
+template <class F> TCG_FN F xe_hot_of(const CellC<F>& c, F lt) {
+  F eHe = m_exp((F(4.45) - lt) * F(1.0 / 0.06));
+  F xeHe = F(0.1) * (F(1) / (F(1) + eHe) + F(1) / (F(1) + eHe * F(4160.262005375057)));  // exp(25/3)
+  F xeMet = F(0.012) * logistic((lt - F(5.5)) * F(4));
+  return xeHe + c.Zg * xeMet;
+}
+
 template <class F> TCG_BIG ChemT<F> chem_T(const CellC<F>& c, F T, unsigned flags) {
   TCG_COUNT(chem_T);
   ChemT<F> b;
@@ -269,13 +279,7 @@ template <class F> TCG_BIG ChemT<F> chem_T(const CellC<F>& c, F T, unsigned flag
   b.arrC = F(4.67e-12) * m_exp(F(-0.6) * lT300);
   b.kCpH2 = F(4.0e-16) * m_exp(F(-0.2) * lT300);
   b.xMH_T = m_exp(F(0.345) * lT300) * F(2041.2414523193154);  // 1/sqrt(2.4e-7 (T/300)^-0.69)
-  F lt = b.lnT * F(0.43429448190325176);  // log10 T
-  // the two He steps differ by a constant shift of the logistic's argument:
-  // exp(-(lt - 4.95)/0.06) = exp(-(lt - 4.45)/0.06) exp(0.5/0.06)
-  F eHe = m_exp((F(4.45) - lt) * F(1.0 / 0.06));
-  F xeHe = F(0.1) * (F(1) / (F(1) + eHe) + F(1) / (F(1) + eHe * F(4160.262005375057)));  // exp(25/3)
-  F xeMet = F(0.012) * logistic((lt - F(5.5)) * F(4));
-  b.xe_hot = xeHe + c.Zg * xeMet;
+  b.xe_hot = xe_hot_of(c, b.lnT * F(0.43429448190325176));  // at log10 T
   b.wdH3T = F(WDH3) * m_exp(F(WDH4) * b.lnT);
   b.wdHex = F(-WDH5) - F(WDH6) * b.lnT;
   b.wdC3T = F(WDC3) * m_exp(F(WDC4) * b.lnT);
@@ -298,6 +302,35 @@ template <class F> struct CoolT {
   F cie;               // S-weighted CIE term: Lambda_He + Z'_g Lambda_metal
 };
 
+// Sums of several temperature factors in the cooling blocks, shared by cool_T and by
+// temp_blocks_step (which evaluates them afresh at the stepped temperature).
+// Ly-alpha (Eq. e:k_lya): E_21 5.31e-8 T4^0.15 / (1 + (T4/5)^0.65) exp(-11.84/T4) with
+// E_21/k_B = 1.184e5 K, from ln(T/1e4) and 1e4/T.
+template <class F> TCG_FN F lya_of(F lT4, F invT4) {
+  return F(1.184e5 * KB * 5.31e-8) * m_exp(F(0.15) * lT4 - F(11.84) * invT4) /
+         (F(1) + m_exp(F(0.65) * (lT4 - F(1.6094379124341003))));
+}
+// free-free Gaunt factor at log10 T = lt
+template <class F> TCG_FN F gff_of(F lt) {
+  F dg = F(5.5) - lt;
+  return F(1.1) + F(0.34) * m_exp(-dg * dg * F(1.0 / 3.0));
+}
+// H2 ro-vibrational LTE rate per molecule from ln(T/1000) and 1000/T (T clamped to
+// [10, 1e4] K by the caller): rotational and vibrational parts
+template <class F> TCG_FN F rovib_lte_of(F lT3, F iT3) {
+  F q = F(0.13) * iT3;
+  F Lrot = F(9.5e-22) * m_exp(F(3.76) * lT3 - q * q * q) / (F(1) + F(0.12) * m_exp(F(2.1) * lT3)) +
+           F(3e-24) * m_exp(F(-0.51) * iT3);
+  F Lvib = F(6.7e-19) * m_exp(F(-5.86) * iT3) + F(1.6e-18) * m_exp(F(-11.7) * iT3);
+  return Lrot + Lvib;
+}
+// CIE cooling of He and metals (before the S weighting) at log10 T = lt
+template <class F> TCG_FN F cie_of(const CellC<F>& c, F lt) {
+  F z1 = (lt - F(5.0)) * F(1.0 / 0.15), z2 = (lt - F(5.35)) * F(1.0 / 0.28), z3 = (lt - F(6.3)) * F(1.0 / 0.35);
+  return F(2.0e-23) * m_exp(F(-0.5) * z1 * z1) +
+         c.Zg * (F(5.4e-22) * m_exp(F(-0.5) * z2 * z2) + F(5.0e-23) * m_exp(F(-0.5) * z3 * z3));
+}
+
 template <class F> TCG_BIG CoolT<F> cool_T(const CellC<F>& c, const ChemT<F>& b, unsigned flags) {
   TCG_COUNT(cool_T);
   CoolT<F> k;
@@ -308,13 +341,9 @@ template <class F> TCG_BIG CoolT<F> cool_T(const CellC<F>& c, const ChemT<F>& b,
   k.eps_num = F(5.22) + F(2.25) * m_exp(F(0.147) * lnT);
   F lT4 = lnT - F(9.210340371976184);
   F invT4 = F(1e4) * invT;
-  // Ly-alpha: 5.31e-8 T4^0.15 / (1 + (T4/5)^0.65) exp(-11.84/T4), E_21/k_B = 1.184e5 K
-  k.lyaE = F(1.184e5 * KB * 5.31e-8) * m_exp(F(0.15) * lT4 - F(11.84) * invT4) /
-           (F(1) + m_exp(F(0.65) * (lT4 - F(1.6094379124341003))));
+  k.lyaE = lya_of(lT4, invT4);
   F lt = lnT * F(0.43429448190325176);
-  F dg = F(5.5) - lt;
-  F gff = F(1.1) + F(0.34) * m_exp(-dg * dg * F(1.0 / 3.0));
-  k.ffrr = F(1.42e-27) * b.sqT * gff + b.arr * F(KB) * T * (F(0.684) - F(0.0416) * lT4);
+  k.ffrr = F(1.42e-27) * b.sqT * gff_of(lt) + b.arr * F(KB) * T * (F(0.684) - F(0.0416) * lT4);
   // C+ 158 um: n_e,crit = 53 T4^1/2, n_H,crit = 3e3 T2^(-0.1281 - 0.0087 ln T2), A = 2.3e-6
   F lT2 = lnT - F(4.605170185988092);
   k.cpke = F(2.3e-6 / 53.0 * 100.0) * b.sqT * invT;  // / (53 T^1/2 / 100)
@@ -345,11 +374,7 @@ template <class F> TCG_BIG CoolT<F> cool_T(const CellC<F>& c, const ChemT<F>& b,
     k.rvLlow = m_exp(poly * F(LN10));
     F lT3 = lnTc - F(6.907755278982137);
     F iT3 = F(1000) / m_min(m_max(T, F(10)), F(1e4));  // 1/T3 = exp(-lT3)
-    F q = F(0.13) * iT3;
-    F Lrot = F(9.5e-22) * m_exp(F(3.76) * lT3 - q * q * q) / (F(1) + F(0.12) * m_exp(F(2.1) * lT3)) +
-             F(3e-24) * m_exp(F(-0.51) * iT3);
-    F Lvib = F(6.7e-19) * m_exp(F(-5.86) * iT3) + F(1.6e-18) * m_exp(F(-11.7) * iT3);
-    k.rvLLTE = Lrot + Lvib;
+    k.rvLLTE = rovib_lte_of(lT3, iT3);
   }
   F st10 = m_sqrt(T * F(0.1));
   k.coA = F(4e-27) * (T * F(0.1)) * st10;
@@ -363,11 +388,104 @@ template <class F> TCG_BIG CoolT<F> cool_T(const CellC<F>& c, const ChemT<F>& b,
   if (flags & FL_NO_CIE) {
     k.cie = F(0);
   } else {
-    F z1 = (lt - F(5.0)) * F(1.0 / 0.15), z2 = (lt - F(5.35)) * F(1.0 / 0.28), z3 = (lt - F(6.3)) * F(1.0 / 0.35);
-    k.cie = F(2.0e-23) * m_exp(F(-0.5) * z1 * z1) +
-            c.Zg * (F(5.4e-22) * m_exp(F(-0.5) * z2 * z2) + F(5.0e-23) * m_exp(F(-0.5) * z3 * z3));
+    k.cie = cie_of(c, lt);
   }
   return k;
+}
+
+// The temperature blocks at T1 = T + dT from those at T, for the forward-difference
+// Jacobian's temperature column (dT ~ 1e-7 T).  A factor C exp(a ln T + b/T) moves by
+// its logarithmic derivative, f(T1) = f(T) (1 + (a + b/T) dT/T); the factors that are
+// sums of several such terms (the hot-gas electrons, Ly-alpha, the Gaunt factor, the H2
+// LTE rate, CIE) and the products of stepped factors are evaluated at T1.  The neglected
+// second-order term is ~((a + b/T) dT/T)^2 / 2 relative, far below the difference's
+// own (a + b/T) dT/T, so the column agrees with the one from chem_T and cool_T at T1 to
+// the forward difference's truncation error: 13 exponentials instead of 38.
+template <class F>
+TCG_BIG void temp_blocks_step(const CellC<F>& c, const ChemT<F>& b, const CoolT<F>& k, F T1, unsigned flags,
+                              ChemT<F>& o, CoolT<F>& ok) {
+  TCG_COUNT(temp_step);
+  const F T = b.T, iT = b.invT;
+  const F dT = T1 - T;
+  const F u = dT * iT;   // dT / T
+  const F ui = u * iT;   // dT / T^2
+  // ---- chemistry block
+  o.T = T1;
+  o.lnT = b.lnT + u;
+  o.sqT = b.sqT + b.sqT * (F(0.5) * u);
+  o.invT = iT - iT * u;
+  o.S = b.S + b.S * (F(1) - b.S) * (F(10.0 / 1.5e4) * dT);
+  if (flags & FL_CONST_KGR) {
+    o.kgr = b.kgr;
+  } else {
+    // k_gr = K s2 / D with s2 = sqrt(T/100), T2 = T/100, D = 1 + 0.4 s2 + 0.2 T2 + 0.08 T2^2
+    F s2 = b.sqT * F(0.1), T2 = T * F(0.01);
+    F D = F(1) + F(0.4) * s2 + F(0.2) * T2 + F(0.08) * T2 * T2;
+    F dD = F(0.2) * s2 * iT + F(0.002) + F(0.0016) * T2;  // dD/dT
+    o.kgr = b.kgr + b.kgr * (F(0.5) * u - dD * dT / D);
+  }
+  F lT4 = b.lnT - F(9.210340371976184);
+  o.arr = b.arr + b.arr * ((F(-0.8163) - F(0.0416) * lT4) * u);
+  F c3s = b.sqT * F(0.003162277660168379);
+  o.kci = b.kci + b.kci * ((F(0.5) - F(0.5) * c3s / (F(1) + c3s)) * u + F(157809.1) * ui);
+  o.kcdH = b.kcdH + b.kcdH * (F(0.5) * u + F(63593.0) * ui);
+  o.kcdH2 = b.kcdH2 + b.kcdH2 * (F(4.1881) * u + F(54657.4) * ui -
+                                 F(5.6881 * 6.761e-6) * dT / (F(1) + F(6.761e-6) * T));
+  o.arrC = b.arrC - b.arrC * (F(0.6) * u);
+  o.kCpH2 = b.kCpH2 - b.kCpH2 * (F(0.2) * u);
+  o.xMH_T = b.xMH_T + b.xMH_T * (F(0.345) * u);
+  F lt1 = o.lnT * F(0.43429448190325176);
+  o.xe_hot = xe_hot_of(c, lt1);
+  o.wdH3T = b.wdH3T + b.wdH3T * (F(WDH4) * u);
+  o.wdHex = b.wdHex - F(WDH6) * u;
+  o.wdC3T = b.wdC3T + b.wdC3T * (F(WDC4) * u);
+  o.wdCex = b.wdCex - F(WDC6) * u;
+  // ---- cooling block
+  ok.fcA = k.fcA + k.fcA * (F(0.5) * u + F(1000.0) * ui);
+  F T12 = T + F(1200.0);
+  ok.fcB = k.fcB + k.fcB * (F(0.5) * u + F(18100.0) * dT / (T12 * T12));
+  ok.eps_num = k.eps_num + (k.eps_num - F(5.22)) * (F(0.147) * u);
+  F lT4_1 = o.lnT - F(9.210340371976184);
+  ok.lyaE = lya_of(lT4_1, F(1e4) * o.invT);
+  ok.ffrr = F(1.42e-27) * o.sqT * gff_of(lt1) + o.arr * F(KB) * T1 * (F(0.684) - F(0.0416) * lT4_1);
+  ok.cpke = F(2.3e-6 / 53.0 * 100.0) * o.sqT * o.invT;
+  F lT2 = b.lnT - F(4.605170185988092);
+  ok.cpkH = k.cpkH + k.cpkH * ((F(0.1281) + F(0.0174) * lT2) * u);
+  ok.cpb = k.cpb + k.cpb * (F(91.25) * ui);
+  const F sO = F(-0.2622274154608984), sC = F(-0.22834652828762741);  // as in cool_T
+  ok.ok10 = k.ok10 - k.ok10 * (sO * u);
+  ok.ob1 = k.ob1 + k.ob1 * (F(227.7) * ui);
+  ok.ob2 = k.ob2 + k.ob2 * (F(326.6) * ui);
+  ok.ob21 = k.ob21 + k.ob21 * (F(326.6 - 227.7) * ui);
+  ok.ck10 = k.ck10 - k.ck10 * (sC * u);
+  ok.cb1 = k.cb1 + k.cb1 * (F(23.6) * ui);
+  ok.cb2 = k.cb2 + k.cb2 * (F(62.4) * ui);
+  ok.cb21 = k.cb21 + k.cb21 * (F(62.4 - 23.6) * ui);
+  if (flags & FL_NO_ROVIB) {
+    ok.rvLlow = k.rvLlow; ok.rvLLTE = k.rvLLTE;
+  } else {
+    // L_low = 10^poly(log10 T): d ln L_low / dT = poly'(log10 T) / T inside the clamp
+    // [10, 1e4] K, zero outside
+    if (b.lnT > F(2.302585092994046) && b.lnT < F(9.210340371976184)) {
+      F x = b.lnT * F(0.43429448190325176);
+      F dpoly = F(97.59) + x * (F(2 * -48.05) + x * (F(3 * 10.80) + x * F(4 * -0.9032)));
+      ok.rvLlow = k.rvLlow + k.rvLlow * (dpoly * u);
+    } else {
+      ok.rvLlow = k.rvLlow;
+    }
+    F lnTc1 = m_min(m_max(o.lnT, F(2.302585092994046)), F(9.210340371976184));
+    ok.rvLLTE = rovib_lte_of(lnTc1 - F(6.907755278982137), F(1000) / m_min(m_max(T1, F(10)), F(1e4)));
+  }
+  ok.coA = k.coA + k.coA * (F(1.5) * u);
+  ok.coN = k.coN + k.coN * (F(0.5) * u);
+  ok.grT = k.grT + k.grT * (F(0.94) * u);
+  ok.grB = k.grB - k.grB * (F(0.068) * u);
+  // nebular: ln f = ln 3.68e-23 + LN10 poly(lT4) - 3.86e4 / T - 0.5 lT4
+  F dpn = F(-5.86e-1) + lT4 * (F(2 * 8.16e-1) + lT4 * (F(3 * -5.05e-1) + lT4 * (F(4 * 1.18e-1) +
+          lT4 * (F(5 * 7.66e-3) + lT4 * F(6 * -5.08e-3)))));
+  ok.nebT = k.nebT + k.nebT * ((F(LN10) * dpn - F(0.5)) * u + F(3.86e4) * ui);
+  ok.nebX = k.nebX - F(0.12) * u;
+  ok.cie = (flags & FL_NO_CIE) ? F(0) : cie_of(c, lt1);
 }
 
 // ------------------------------------------------------------------ C/O/e equilibrium (Secs. 3.2, 3.3)

@@ -22,7 +22,7 @@
 
 namespace wc {
 struct Calls {
-  long long chem_T, cool_T, equil, equil_it, dust, dust_it, source;
+  long long chem_T, cool_T, temp_step, equil, equil_it, dust, dust_it, source;
   long long newton64_it, chord64_it, newton32_it, polish_it, substep_paper, picard_it;
 };
 Calls calls[3];  // [0] FP64, [1] FP32, [2] df64 (double-float)
@@ -100,7 +100,7 @@ int main(int argc, char** argv) {
   DevParams p{1.0, 2.73, 1.0, 1.0, 1.0 / 3.0, 0.1, 1e-3, 1e-12, 1e-6, 1.0, 50, 1000000, 0};  // library defaults
 
   // ---- pass 1: cost per call of each block (FP64), averaged over the sample's cells
-  OpCnt c_chem{}, c_cool{}, c_src{}, c_eq_set{}, c_eq_it{}, c_dust_set{}, c_dust_it{};
+  OpCnt c_chem{}, c_cool{}, c_step{}, c_src{}, c_eq_set{}, c_eq_it{}, c_dust_set{}, c_dust_it{};
   long long nb = 0;
   for (int64_t i = 0; i < n; i += (n > 256 ? n / 256 : 1), ++nb) {
     CellC<double> cd = make_cell(col(0)[i], col(1)[i], col(2)[i], col(3)[i], col(4)[i], col(5)[i], col(6)[i],
@@ -112,6 +112,17 @@ int main(int argc, char** argv) {
     OpCnt o1 = g_ops;
     CoolT<CntD> k = cool_T(c, b, 0u);
     OpCnt o2 = g_ops;
+    {  // the temperature blocks stepped to T + 1e-7 T (the Jacobian's temperature column)
+      ChemT<CntD> bT;
+      CoolT<CntD> kT;
+      const OpCnt s0 = g_ops;
+      temp_blocks_step(c, b, k, CntD(T * (1.0 + 1e-7)), 0u, bT, kT);
+      const OpCnt d = diff(g_ops, s0);
+      c_step.add += d.add; c_step.mul += d.mul; c_step.div += d.div;
+      c_step.sqrt += d.sqrt; c_step.exp += d.exp; c_step.log += d.log;
+      g_ops = s0;  // keep the differences below to the blocks they time
+      o2 = g_ops;
+    }
     // C/O/e root: a cold solve (k iterations) and a warm one from the root (1 iteration)
     long long it0 = wc::calls[0].equil_it;
     Equil<CntD> q = equilibrium(c, b, CntD(x2), CntD(xp), CntD(-1.0));
@@ -166,6 +177,7 @@ int main(int argc, char** argv) {
   printf("{\n  \"cells\": %lld,\n  \"dt_s\": %.6e,\n", (long long)n, dt);
   print_ops("cost_chem_T", c_chem, inv, true);
   print_ops("cost_cool_T", c_cool, inv, true);
+  print_ops("cost_temp_step", c_step, inv, true);
   print_ops("cost_source", c_src, inv, true);
   print_ops("cost_equil_setup", c_eq_set, inv, true);
   print_ops("cost_equil_iter", c_eq_it, inv, true);
@@ -208,19 +220,20 @@ int main(int argc, char** argv) {
     const wc::Calls& k = wc::calls[0];
     const wc::Calls& f = wc::calls[1];
     const wc::Calls& h = wc::calls[2];
-    printf("  \"mode%d\": {\"substeps\": %.4f, \"fp64\": {\"chem_T\": %.4f, \"cool_T\": %.4f, \"equil\": %.4f, "
+    printf("  \"mode%d\": {\"substeps\": %.4f, \"fp64\": {\"chem_T\": %.4f, \"cool_T\": %.4f, \"temp_step\": %.4f, \"equil\": %.4f, "
            "\"equil_it\": %.4f, \"dust\": %.4f, \"dust_it\": %.4f, \"source\": %.4f, \"newton64_it\": %.4f, "
            "\"chord64_it\": %.4f, \"newton32_it\": %.4f, \"polish_it\": %.4f, \"substep_paper\": %.4f, "
            "\"picard_it\": %.4f}, ",
-           mode, (double)nsub / n, (double)k.chem_T / n, (double)k.cool_T / n, (double)k.equil / n,
+           mode, (double)nsub / n, (double)k.chem_T / n, (double)k.cool_T / n, (double)k.temp_step / n, (double)k.equil / n,
            (double)k.equil_it / n, (double)k.dust / n, (double)k.dust_it / n, (double)k.source / n,
            (double)k.newton64_it / n, (double)k.chord64_it / n, (double)k.newton32_it / n, (double)k.polish_it / n,
            (double)k.substep_paper / n, (double)k.picard_it / n);
     for (int cl = 1; cl <= 2; ++cl) {
       const wc::Calls& x = (cl == 1) ? f : h;
-      printf("\"%s\": {\"chem_T\": %.4f, \"cool_T\": %.4f, \"equil\": %.4f, \"equil_it\": %.4f, \"dust\": %.4f, "
+      printf("\"%s\": {\"chem_T\": %.4f, \"cool_T\": %.4f, \"temp_step\": %.4f, \"equil\": %.4f, \"equil_it\": %.4f, \"dust\": %.4f, "
              "\"dust_it\": %.4f, \"source\": %.4f}%s",
-             (cl == 1) ? "fp32" : "df64", (double)x.chem_T / n, (double)x.cool_T / n, (double)x.equil / n,
+             (cl == 1) ? "fp32" : "df64", (double)x.chem_T / n, (double)x.cool_T / n, (double)x.temp_step / n,
+             (double)x.equil / n,
              (double)x.equil_it / n, (double)x.dust / n, (double)x.dust_it / n, (double)x.source / n,
              (cl == 1) ? ", " : "");
     }

@@ -53,8 +53,9 @@ LINALG = {
 }
 DF64_FP32_INST = {"add": 11, "mul": 7, "div": 28, "sqrt": 20, "exp": 125, "log": 170}
 CLASSES = ("add", "mul", "div", "sqrt", "exp", "log")
-BLOCKS = {"chem_T": "cost_chem_T", "cool_T": "cost_cool_T", "source": "cost_source", "equil": "cost_equil_setup",
-          "equil_it": "cost_equil_iter", "dust": "cost_dust_setup", "dust_it": "cost_dust_iter"}
+BLOCKS = {"chem_T": "cost_chem_T", "cool_T": "cost_cool_T", "temp_step": "cost_temp_step", "source": "cost_source",
+          "equil": "cost_equil_setup", "equil_it": "cost_equil_iter", "dust": "cost_dust_setup",
+          "dust_it": "cost_dust_iter"}
 
 
 def build(tmp: str) -> str:
