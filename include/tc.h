@@ -96,11 +96,11 @@ typedef struct tc_params {
                                   warp-cooperative kernels of modes TC_MODE_NEWTON_FP64 and TC_MODE_MIXED,
                                   whose four lanes evaluate the four points of each forward-difference
                                   Jacobian at once (tc_step and tc_step_host only; other modes and
-                                  tc_step_batch use 1).  0 (default): for TC_MODE_NEWTON_FP64 4 when the
-                                  cells times 4 fit the cooperative kernel's resident lanes at once
-                                  (launches too small to fill the GPU, whose time is the latency of the
-                                  slowest cells), else 1, unless tc_autotune has recorded a choice for
-                                  the launch's size class. */
+                                  tc_step_batch use 1).  0 (default): for TC_MODE_NEWTON_FP64 and
+                                  TC_MODE_MIXED 4 when the cells times 4 fit the cooperative kernel's
+                                  resident lanes at once (launches too small to fill the GPU, whose
+                                  time is the latency of the slowest cells), else 1, unless
+                                  tc_autotune has recorded a choice for the launch's size class. */
 } tc_params;
 
 typedef struct tc_fields {
