@@ -511,8 +511,8 @@ template <class F> TCG_BIG Equil<F> equilibrium(const CellC<F>& c, const ChemT<F
   const F num = c.xCtot * src;
   const F Gs = c.G0 * b.sqT;
   const F agr0 = F(1e-14 * WDC0) * c.Zd;
-  // x_C+(x) and its derivative
-  auto xcp = [&](F x, F& dxcp, F& lp) -> F {
+  // x_C+(x), its derivative, ln psi(x) and d ln psi / dx
+  auto xcp = [&](F x, F& dxcp, F& lp, F& dlp) -> F {
     F ne = x * c.n;
     F psi = Gs / m_max(ne, F(1e-30)) + F(50);
     lp = m_log(psi);
@@ -522,11 +522,10 @@ template <class F> TCG_BIG Equil<F> equilibrium(const CellC<F>& c, const ChemT<F
     F invD = F(1) / D;
     F agr = agr0 * invD;
     F den = sink0 + (agr + b.arrC * x) * c.n;
-    // dD/dx = dD/dpsi dpsi/dx, with psi dD/dpsi = C1 (C2 pa (1 + pb) + pa C5' pb) and
-    // dpsi/dx = -(psi - 50)/x when ne > floor; d agr/dx = -agr dD/dx / D
-    F dDdx = (ne > F(1e-30))
-                 ? -F(WDC1) * (F(WDC2) * pa * (F(1) + pb) + pa * b.wdCex * pb) * (psi - F(50)) / (psi * x)
-                 : F(0);
+    // dD/dx = dD/d ln psi  d ln psi/dx, with dD/d ln psi = C1 (C2 pa (1 + pb) + pa C5' pb)
+    // and d ln psi/dx = -(psi - 50)/(psi x) when ne > floor; d agr/dx = -agr dD/dx / D
+    dlp = (ne > F(1e-30)) ? -(psi - F(50)) / (psi * x) : F(0);
+    F dDdx = F(WDC1) * (F(WDC2) * pa * (F(1) + pb) + pa * b.wdCex * pb) * dlp;
     F dagr = -agr * invD * dDdx;
     F invden = F(1) / den;
     F r = num * invden;
@@ -535,6 +534,9 @@ template <class F> TCG_BIG Equil<F> equilibrium(const CellC<F>& c, const ChemT<F
   };
   F lo = a0, hi = a0 + w * c.xCtot;
   F xe;
+  // the last evaluation of the iteration (point, x_C+, derivative, ln psi, d ln psi/dx)
+  bool have_ev = false;
+  F x_ev = F(0), r_ev = F(0), d_ev = F(0), lp_ev = F(0), dlp_ev = F(0);
   if (!(hi > lo) || !(num > F(0))) {
     xe = a0;
   } else {
@@ -543,8 +545,11 @@ template <class F> TCG_BIG Equil<F> equilibrium(const CellC<F>& c, const ChemT<F
     xe = x;
     for (int it = 0; it < 100; ++it) {
       TCG_COUNT(equil_it);
-      F d, lpx;
-      F g = x - a0 - w * xcp(x, d, lpx);
+      F d, lpx, dlpx;
+      const F r = xcp(x, d, lpx, dlpx);
+      x_ev = x; r_ev = r; d_ev = d; lp_ev = lpx; dlp_ev = dlpx;
+      have_ev = true;
+      F g = x - a0 - w * r;
       if (g == F(0)) { xe = x; break; }
       if (g > F(0)) hi = x; else lo = x;
       F gp = F(1) - w * d;
@@ -564,10 +569,20 @@ template <class F> TCG_BIG Equil<F> equilibrium(const CellC<F>& c, const ChemT<F
     }
   }
   q.xe = xe;
-  // the final evaluation's ln psi is log_psi(c, b, xe) to the bit (same operations):
-  // source() takes it from here
-  F dd;
-  q.xCp = xcp(xe, dd, q.lpsi);
+  // x_C+ and ln psi at the root (source() takes ln psi from here): the last evaluation
+  // stepped to xe to first order when that step is small, |xe - x| <= 1e-6 xe.  That is
+  // the solve's final Newton step: below the root tolerance when converged, so exact to
+  // rounding, and ~1e-7 xe after the single capped step of the Jacobian's perturbed
+  // evaluations, leaving ~1e-14 relative.  Otherwise (no iteration, or a solve stopped
+  // far from its root) a fresh evaluation at xe.
+  const F dxe = xe - x_ev;
+  if (have_ev && m_abs(dxe) <= F(1e-6) * xe) {
+    q.xCp = r_ev + d_ev * dxe;
+    q.lpsi = lp_ev + dlp_ev * dxe;
+  } else {
+    F dd, dl;
+    q.xCp = xcp(xe, dd, q.lpsi, dl);
+  }
   F fr = m_max((c.xCtot > F(0)) ? q.xCp / c.xCtot : F(0), xHp);
   q.xCO = c.xCtot * F(2) * xH2 * (F(1) - fr) / (F(1) + c.rCO2);  // Eq. e:CO
   q.xC = c.xCtot - q.xCp - q.xCO;
@@ -658,7 +673,7 @@ template <class F> TCG_BIG Src<F> source(const CellC<F>& c, const ChemT<F>& b, c
   Src<F> s;
   const F n = c.n;
   const F xe = q.xe;
-  const F lp = q.lpsi;  // log_psi(c, b, xe), from the equilibrium solve
+  const F lp = q.lpsi;  // log_psi(c, b, xe) from the equilibrium solve (to ~1e-14 relative)
   const HRate<F> r = h_rates(c, b, xH2, xH, xe, lp);
   s.form = r.kn * xH;
   s.dest = r.DH2 * xH2;
