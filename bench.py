@@ -44,13 +44,13 @@ FP64_NOMINAL_TFLOPS = 1.25
 
 STATE_KEYS = ("T", "xH2", "xHp")
 # DRAM bytes per cell of one k_step<1> launch on the 128^3 slab in the benchmark's
-# autotuned shape (128 threads x 912 blocks, 768 resident threads per SM), from ncu
+# autotuned shape (64 threads x 1824 blocks, 768 resident threads per SM), from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass,
-# profiles/k_step_fp64_slab128.md): 20.62 GB read + 29.68 GB written for 2,097,152
+# profiles/k_step_fp64_slab128.md): 20.07 GB read + 29.21 GB written for 2,097,152
 # cells.  Almost all of it is the per-thread stack (spills at the 80-register cap and
 # the structs passed to the out-of-line physics): ~3 KB per thread for 768 resident
 # threads per SM is ~350 MB, almost three times L2.  The cells' own data are 152 B.
-TRAFFIC_BYTES_PER_CELL = None  # the kernel changed since the last capture
+TRAFFIC_BYTES_PER_CELL = 23499.0
 
 
 def parse():

@@ -265,8 +265,8 @@ static int coop_occupancy(int kmode, int block) {
 // tc_params values win; otherwise the shape tc_autotune recorded for the launch's size
 // class; otherwise 128 threads, the occupancy limit, and for modes 1 and 2 four lanes per
 // cell when every cell's four lanes fit the cooperative kernel's resident lanes at once
-// (4096 random states: FP64 Newton 73.5 ms against 113.1 ms with one lane, mixed 47.1
-// against 56.5 ms; the mixed solve builds one FP32 Jacobian per solve and spends most of
+// (4096 random states: FP64 Newton 73.1 ms against 108.8 ms with one lane, mixed 43.7
+// against 55.7 ms; the mixed solve builds one FP32 Jacobian per solve and spends most of
 // its time in the df64 polish and substep-start sources, which four lanes do not
 // shorten).  The persistent grid never exceeds the blocks that hold one lane per cell
 // lane.
