@@ -75,6 +75,7 @@ int main(int argc, char** argv) {
   const double temps[11] = {12.0, 30.0, 100.0, 300.0, 1e3, 3e3, 9e3, 3e4, 1e5, 1e6, 1e7};
   const unsigned flag_sets[2] = {0u, FL_CONST_KGR | FL_NO_ROVIB | FL_NO_CIE};
   double e_chem[NCHEM] = {0}, e_cool[NCOOL] = {0};
+  double e_lpsi = 0, e_cxe = 0, e_cxcp = 0, e_clp = 0;
   long long checks = 0;
   for (int64_t i = 0; i < n; ++i) {
     const CellC<double> c = make_cell(col(0)[i], col(1)[i], col(2)[i], col(3)[i], col(4)[i], col(5)[i], col(6)[i],
@@ -98,11 +99,21 @@ int main(int argc, char** argv) {
         fe = reinterpret_cast<const double*>(&ke);
         fs = reinterpret_cast<const double*>(&ks);
         for (int j = 0; j < NCOOL; ++j) upd(e_cool[j], field_err(f0[j], fe[j], fs[j]));
+        // C/O/e root: converged from scratch, then capped at one step from 1e-7 off
+        const double x2 = col(10)[i], xp = col(11)[i];
+        const Equil<double> q = equilibrium(c, b, x2, xp, -1.0);
+        const double lp = log_psi(c, b, q.xe);
+        upd(e_lpsi, std::fabs(q.lpsi - lp) / std::fmax(std::fabs(lp), 1e-300));
+        const Equil<double> qc = equilibrium(c, b, x2, xp, q.xe * (1.0 + 1e-7), 1);
+        upd(e_cxe, std::fabs(qc.xe - q.xe) / q.xe);
+        upd(e_cxcp, std::fabs(qc.xCp - q.xCp) / std::fmax(std::fabs(q.xCp), 1e-300));
+        upd(e_clp, std::fabs(qc.lpsi - q.lpsi) / std::fmax(std::fabs(q.lpsi), 1e-300));
         ++checks;
       }
     }
   }
-  printf("{\"checks\": %lld", checks);
+  printf("{\"checks\": %lld, \"lpsi_converged\": %.3e, \"capped_xe\": %.3e, \"capped_xCp\": %.3e, "
+         "\"capped_lpsi\": %.3e", checks, e_lpsi, e_cxe, e_cxcp, e_clp);
   for (int j = 0; j < NCHEM; ++j) printf(", \"%s\": %.3e", kChemNames[j], e_chem[j]);
   for (int j = 0; j < NCOOL; ++j) printf(", \"%s\": %.3e", kCoolNames[j], e_cool[j]);
   printf("}\n");

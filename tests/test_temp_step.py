@@ -7,6 +7,9 @@ second-order term (normalised error below 1), at the cells' own temperatures and
 sweep from 12 K to 1e7 K, with the physics switches off and on.  A wrong coefficient,
 sign or missing term in one field's logarithmic derivative makes its error of order
 1/|g| (1e3 to 1e7 here).
+
+The same program checks the C/O/e root's x_C+ and ln psi, which the root solve takes
+from its last evaluation stepped to the root instead of evaluating them afresh.
 """
 import json
 import os
@@ -21,6 +24,7 @@ import synthgen
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2210_08024_gb300", "csrc")
 IN_KEYS = ("n", "chi_pe", "chi_lw", "f_h2", "f_c", "F_lyc", "xi", "Zg", "Zd", "T", "xH2", "xHp")
+ROOT_BOUNDS = {"lpsi_converged": 1e-14, "capped_xe": 1e-13, "capped_xCp": 1e-12, "capped_lpsi": 1e-12}
 
 
 @pytest.fixture(scope="module")
@@ -56,5 +60,11 @@ def test_stepped_blocks_match_the_blocks_at_t_plus_dt(exe, tmp_path, workload):
     cells = _slab() if workload == "slab" else synthgen.cells_4096(n=400, key=42)
     r = _run(exe, cells, tmp_path / "cells.bin")
     assert r.pop("checks") == 400 * 12 * 2
+    root = {k: r.pop(k) for k in ROOT_BOUNDS}
     bad = {k: v for k, v in r.items() if not v < 1.0}
     assert not bad, bad
+    # the C/O/e root's x_C+ and ln psi, stepped from the solve's last evaluation: to
+    # rounding when converged, ~1e-14 after one capped step from 1e-7 off the root (a
+    # wrong sign or derivative in the step would leave ~1e-7)
+    for k, bound in ROOT_BOUNDS.items():
+        assert root[k] <= bound, (k, root[k], bound)
