@@ -24,7 +24,8 @@ each costs this many FP32-pipe instructions, counted from tc_df64.cuh (error-fre
 transformations included; exp and log with their call overhead):
     add 11, mul 7, div 28, sqrt 20, exp 125, log 170
 
-    python -m paper_2210_08024_gb300.work
+    python -m paper_2210_08024_gb300.work               # count, write work_slab128.json
+    python -m paper_2210_08024_gb300.work --breakdown   # FP64 slots per building block
 """
 from __future__ import annotations
 
@@ -138,5 +139,37 @@ def main(sample: int = 8192):
     return res
 
 
+# FMA-slot cost per operation class, as tc_peak measures it on a GB300 (the benchmark
+# measures them again in each run; these are the values of one run, for the breakdown)
+SLOT_WEIGHTS = {"add": 1.0, "mul": 1.0, "div": 5.67, "sqrt": 8.61, "exp": 16.0, "log": 30.2}
+
+
+def breakdown(res: dict, mode: str = "mode1") -> list:
+    """FP64 FMA slots per cell of one mode by building block (calls x cost per call, and
+    the hand-counted dense algebra of each iteration), largest first: where the FP64
+    work of the step goes."""
+    raw = res["raw"]
+    calls = raw[mode]["fp64"]
+    rows = []
+    for blk, key in BLOCKS.items():
+        n = calls.get(blk, 0.0)
+        rows.append((blk, n, n * sum(raw[key][c] * SLOT_WEIGHTS[c] for c in CLASSES)))
+    for blk, la in LINALG.items():
+        n = calls.get(blk, 0.0)
+        rows.append((blk, n, n * sum(v * SLOT_WEIGHTS[c] for c, v in la.items())))
+    rows = [r for r in rows if r[2] > 0.0]
+    return sorted(rows, key=lambda r: -r[2])
+
+
 if __name__ == "__main__":
-    main()
+    if len(sys.argv) > 1 and sys.argv[1] == "--breakdown":
+        with open(OUT) as fh:
+            res = json.load(fh)
+        for mode in ("mode1", "mode0"):
+            rows = breakdown(res, mode)
+            tot = sum(r[2] for r in rows)
+            print("%s: %.0f FMA slots per cell" % (mode, tot))
+            for blk, n, sl in rows:
+                print("  %-12s %7.2f calls  %7.0f slots  %5.1f%%" % (blk, n, sl, 100.0 * sl / tot))
+    else:
+        main()
