@@ -40,3 +40,20 @@ def test_work_counts_cover_every_mode():
     assert work["mode2"]["exp"] == 0 and work["mode2"]["log"] == 0 and work["mode2"]["add"] > 0
     assert all(work["mode2_df64"][k] > 0 for k in ("add", "mul", "div", "exp", "log"))
     assert all(work["mode2_fp32"][k] > 0 for k in ("add", "mul", "div", "exp", "log"))
+
+
+def test_work_breakdown_covers_the_counted_work():
+    import json
+    from paper_2210_08024_gb300 import work
+    with open(work.OUT) as fh:
+        res = json.load(fh)
+    rows = work.breakdown(res, "mode1")
+    names = [r[0] for r in rows]
+    # the FP64 Newton step's blocks, the stepped temperature column among them
+    for blk in ("source", "chem_T", "cool_T", "temp_step", "equil_it", "newton64_it"):
+        assert blk in names
+    # largest first, and the blocks add up to the weighted per-cell count
+    assert all(rows[i][2] >= rows[i + 1][2] for i in range(len(rows) - 1))
+    per_cell = res["per_cell"]["mode1"]
+    total = sum(per_cell[c] * work.SLOT_WEIGHTS[c] for c in work.CLASSES)
+    assert sum(r[2] for r in rows) == pytest.approx(total, rel=1e-3)
